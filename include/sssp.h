@@ -1,0 +1,281 @@
+/*
+ * sssp.h -- C ABI of libsssp, a GB300 (sm_103a) implementation of the hot
+ * path of SP_Async (S. Yadav, A. Khan, "SP_Async: Single Source Shortest Path
+ * in Asynchronous Mode on MPI", arXiv 2103.12012).
+ *
+ * The paper's problem (Sec. I): a directed graph G(V,E) with non-negative
+ * edge costs W and a source S; find the least-cost path from S to every
+ * vertex.  Its method (Sec. III): 1D block partitioning (Sec. III.A), the
+ * Trishla triangle edge prune (Sec. III.B, Algorithm 1), Dijkstra inside each
+ * partition and asynchronous Bellman-Ford-style messages between partitions
+ * (Sec. III.C, SP-Async and DIJKSTRA), stopped by message-count termination
+ * detection (Sec. III.D, ToKa).  On one GPU each partition is owned by a
+ * persistent thread block, a message is a 64-bit atomicMin on the packed word
+ * (distance << 32 | predecessor) of the target vertex plus a bit in the owner
+ * partition's device-memory inbox, and termination is a device-global count
+ * of queued-but-unprocessed vertices.
+ *
+ * Conventions shared by every entry point:
+ *  - Ownership: the caller allocates and owns every buffer, device or host;
+ *    the library allocates no device memory.  Scratch space ("workspace") is
+ *    sized by the matching *_workspace_size query and passed in.
+ *  - Pointers marked "device" must be device memory of the current device;
+ *    "host" pointers are host memory.  Device buffers need 16-byte alignment
+ *    (torch allocations satisfy this).
+ *  - Streams: every call is asynchronous on `stream` (a cudaStream_t, NULL =
+ *    the legacy default stream) unless it says otherwise.  Host-detectable
+ *    argument errors return SSSP_EINVAL (or SSSP_ENOMEM for a workspace that
+ *    is too small) before anything is launched.  Errors found on the device
+ *    (timeout, overflow, bad weight, bad vertex id) are recorded in the
+ *    workspace's status word; sssp_workspace_status() synchronises the stream
+ *    and returns them.
+ *  - Graph format (sssp_graph): CSR with 32-bit offsets and vertex ids; rows
+ *    sorted by head, no self-loops, no parallel edges (sssp_build_csr makes
+ *    this form).  Weights are uint32 >= 1 or float32 > 0 and finite.
+ *  - Values: an unreachable vertex has dist 0xFFFFFFFF (uint32) or +inf
+ *    (float32) and pred 0xFFFFFFFF; the source has dist 0 and pred
+ *    0xFFFFFFFF.  pred[v] is the smallest vertex id u with
+ *    dist(u) + w(u,v) == dist(v) (the canonical predecessor).
+ *  - uint32 distances: a candidate d(u)+w that does not fit below 0xFFFFFFFF
+ *    is discarded and the status becomes SSSP_EOVERFLOW; vertices whose true
+ *    distance does not fit are then reported unreachable.
+ */
+#ifndef SSSP_H
+#define SSSP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* sssp_stream_t; /* identical to cudaStream_t */
+
+typedef enum {
+    SSSP_OK = 0,
+    SSSP_EINVAL = 1,     /* bad argument (host check) or bad vertex id / weight (device check) */
+    SSSP_ENOMEM = 2,     /* workspace smaller than the size query asked for */
+    SSSP_ECUDA = 3,      /* a CUDA runtime call failed */
+    SSSP_ETIMEOUT = 4,   /* a device wait exceeded its limit; outputs are not valid */
+    SSSP_EOVERFLOW = 5,  /* a uint32 path length exceeded 0xFFFFFFFE (see conventions) */
+    SSSP_EINTERNAL = 6,  /* an internal invariant failed */
+    SSSP_EUNSUPPORTED = 7
+} sssp_status;
+
+typedef enum { SSSP_W_U32 = 0, SSSP_W_F32 = 1 } sssp_wtype;
+
+/* A CSR graph in device memory (Sec. III.A: the per-process adjacency Padj,
+ * here one array for all partitions; partition p owns the vertex block
+ * [p*B, min((p+1)*B, V)) with B = ceil(V / partitions)). */
+typedef struct {
+    uint32_t V;              /* vertex count, >= 1 */
+    uint32_t E;              /* edge count */
+    const uint32_t* row_ptr; /* device [V+1], row_ptr[0] = 0, row_ptr[V] = E */
+    const uint32_t* col;     /* device [E], heads, strictly increasing within a row, != tail */
+    const void* w;           /* device [E], uint32 or float32 according to wtype */
+    int32_t wtype;           /* sssp_wtype */
+    uint32_t partitions;     /* P >= 1 (Sec. III.A 1D block partitioning) */
+} sssp_graph;
+
+/* Tuning knobs; a zero field means "default".  None of them changes the
+ * result, only the schedule. */
+typedef struct {
+    uint32_t threads;      /* threads per block of the relaxation kernel: 128..1024, multiple of 32 (default 512) */
+    uint32_t blocks_per_sm;/* persistent blocks per SM (default: as many as fit) */
+    uint32_t tile;         /* most vertices one block takes from its inbox per round: 32..4096 (default 1024) */
+    uint32_t split;        /* blocks sharing one partition, each owning a sub-block of its vertices (default 1) */
+    double delta;          /* bucket width: a round takes inbox vertices with dist < min dist + delta
+                              (default: uint32 -> 4 x mean edge weight estimate 128, float32 -> 1.0) */
+    uint64_t timeout_ns;   /* limit on a block's continuous idle wait (default 20 s) */
+    uint32_t flags;        /* SSSP_FLAG_* */
+    uint32_t reserved;
+    void* ev_relax_begin;  /* cudaEvent_t or NULL: recorded on `stream` right before the relaxation kernel */
+    void* ev_relax_end;    /* cudaEvent_t or NULL: recorded right after it (for timing that kernel alone) */
+} sssp_options;
+
+/* Test hook: start the pending count one above the true value so that the
+ * termination count can never reach zero; the solve must then end with
+ * SSSP_ETIMEOUT after `timeout_ns`, with the device still usable. */
+#define SSSP_FLAG_TEST_HOLD_PENDING 0x1u
+
+/* Device-side counters of the last solve (sssp_workspace_status). */
+typedef struct {
+    uint64_t edges_scanned;    /* relaxations attempted: edges of every processed vertex */
+    uint64_t atomics;          /* 64-bit atomicMin issued after the read-first filter */
+    uint64_t improved;         /* atomicMin that lowered the target's distance */
+    uint64_t activations;      /* inbox bits turned on (vertices queued) */
+    uint64_t rounds;           /* rounds run by all blocks */
+    uint64_t vertices;         /* vertices processed (taken from an inbox) */
+    uint64_t remote_activations; /* activations of a vertex owned by another unit (messages, Alg. 3 send_msg) */
+    uint64_t reserved;
+} sssp_stats;
+
+const char* sssp_status_string(sssp_status s);
+
+/* Library build identity (a constant string). */
+const char* sssp_version(void);
+
+/* ------------------------------------------------------------------ K1 CSR */
+
+/* Workspace bytes needed by sssp_build_csr for V vertices and E_raw input edges. */
+size_t sssp_build_csr_workspace_size(uint32_t V, uint64_t E_raw);
+
+/*
+ * COO -> canonical CSR (the Padj adjacency of Sec. III.A).  Self-loops are
+ * dropped and parallel edges collapsed to their minimum weight (lowest input
+ * index on ties); neither changes any shortest distance.
+ *   src, dst : device [E_raw] uint32 tail/head ids (< V, else SSSP_EINVAL on the device status)
+ *   w        : device [E_raw] weights of type wtype
+ *   row_ptr  : device [V+1] out
+ *   col, w_out, eid : device [E_raw] out (first *E_out entries valid); eid[e] = input index of kept edge e
+ *                     (eid may be NULL)
+ *   E_out    : device [1] out, number of CSR edges
+ *   ws       : device workspace of ws_bytes >= sssp_build_csr_workspace_size(V, E_raw); it also
+ *              holds the status word read by sssp_workspace_status
+ * E_raw must be < 2^32.
+ */
+sssp_status sssp_build_csr(uint32_t V, uint64_t E_raw, const uint32_t* src, const uint32_t* dst, const void* w,
+                           int32_t wtype, uint32_t* row_ptr, uint32_t* col, void* w_out, uint32_t* eid,
+                           uint32_t* E_out, void* ws, size_t ws_bytes, sssp_stream_t stream);
+
+/* ------------------------------------------------------------ K2 partition */
+
+/*
+ * 1D block partition (Sec. III.A, read as B = ceil(V/P), Pid(v) = floor(v/B)).
+ *   bounds : device [P+1] out, bounds[p] = min(p*B, V)
+ *   inter  : device [P] out (may be NULL), edges whose tail is in partition p and head is not --
+ *            the "inter-edges" of Sec. III.D whose product with P is ToKa's message threshold.
+ */
+sssp_status sssp_partition(const sssp_graph* g, uint32_t* bounds, uint64_t* inter, sssp_stream_t stream);
+
+/* ------------------------------------------------------------ K3 Trishla */
+
+/*
+ * Trishla (Sec. III.B, Algorithm 1): edge (u, v_j) is deleted when some
+ * out-neighbour v_i of u has an edge (v_i, v_j) with
+ *     w(u, v_j) > w(u, v_i) + w(v_i, v_j)      (strict; float32 sums rounded once).
+ * mode 0 (local, the paper's E_i): v_i must be in u's partition.  mode 1
+ * (global): any v_i.  Every test reads the unpruned graph, so the result does
+ * not depend on evaluation order.
+ *   keep    : device [E] out, 1 = kept, 0 = deleted
+ *   witness : device [E] out (may be NULL), smallest such v_i, 0xFFFFFFFF for kept edges
+ */
+sssp_status sssp_prune(const sssp_graph* g, int32_t mode, uint8_t* keep, uint32_t* witness, sssp_stream_t stream);
+
+/* Workspace bytes of sssp_compact. */
+size_t sssp_compact_workspace_size(uint32_t V, uint32_t E);
+
+/*
+ * The graph without the edges with keep[e] == 0 (what the relaxation of
+ * Sec. III.C then scans).  row_ptr_out device [V+1]; col_out, w_out,
+ * emap_out device [E] (first *E_out valid); emap_out[k] = index in g of kept
+ * edge k (may be NULL).  E_out device [1].
+ */
+sssp_status sssp_compact(const sssp_graph* g, const uint8_t* keep, uint32_t* row_ptr_out, uint32_t* col_out,
+                         void* w_out, uint32_t* emap_out, uint32_t* E_out, void* ws, size_t ws_bytes,
+                         sssp_stream_t stream);
+
+/* --------------------------------------------------------- K0/K4 solve */
+
+/* Workspace bytes of sssp_solve for graph g and S sources with options opt (may be NULL). */
+size_t sssp_solve_workspace_size(const sssp_graph* g, uint32_t S, const sssp_options* opt);
+
+/*
+ * SP-Async (Sec. III.C, SP-Async and DIJKSTRA; Sec. III.D termination) for S
+ * sources at once, each an independent problem on the same graph.
+ *   sources : device [S] vertex ids (< V)
+ *   dist    : device [S][V] out, uint32 or float32 per g->wtype
+ *   pred    : device [S][V] out (may be NULL), canonical predecessor vertex
+ *   ws      : device workspace >= sssp_solve_workspace_size(g, S, opt)
+ * Launches an init kernel, one persistent cooperative relaxation kernel in
+ * which each block owns (source, partition sub-block) units, and an unpack
+ * kernel.  Needs every block co-resident; returns SSSP_EUNSUPPORTED if the
+ * device cannot hold one block per unit... (it then reuses blocks over
+ * several units, so it only fails if not even one block fits).
+ */
+sssp_status sssp_solve(const sssp_graph* g, const uint32_t* sources, uint32_t S, void* dist, uint32_t* pred,
+                       const sssp_options* opt, void* ws, size_t ws_bytes, sssp_stream_t stream);
+
+/*
+ * Synchronise `stream`, then return the status recorded on the device by the
+ * last call that used workspace `ws` (and clear nothing).  stats (host, may
+ * be NULL) receives that call's counters (zero for calls that keep none).
+ */
+sssp_status sssp_workspace_status(const void* ws, sssp_stream_t stream, sssp_stats* stats);
+
+/* ------------------------------------------------------------ K5 batched */
+
+/* One graph of a batch: its CSR lives inside shared concatenated arrays. */
+typedef struct {
+    uint64_t row_off;  /* offset of this graph's V+1 row_ptr entries in the concatenated row_ptr */
+    uint64_t edge_off; /* offset of this graph's first edge in the concatenated col / w */
+    uint32_t V;        /* vertices (row_ptr values are relative to edge_off) */
+    uint32_t E;        /* edges */
+} sssp_batch_graph;
+
+/* A batch of independent problems (graph, source) over several graphs. */
+typedef struct {
+    uint32_t n_graphs;
+    uint32_t n_problems;
+    const sssp_batch_graph* graphs; /* host [n_graphs] */
+    const uint32_t* prob_graph;     /* host [n_problems], graph index of each problem */
+    const uint32_t* prob_source;    /* host [n_problems], source (graph-local id) */
+    const uint32_t* row_ptr;        /* device, concatenated */
+    const uint32_t* col;            /* device, concatenated, graph-local ids */
+    const void* w;                  /* device, concatenated */
+    int32_t wtype;
+    void* dist;                     /* device out: problem i's V_g values start at out_off(i) = sum_{j<i} V_{graph(j)} */
+    uint32_t* pred;                 /* device out, same layout (may be NULL) */
+} sssp_batch;
+
+/* Workspace bytes of the batched solve. */
+size_t sssp_batch_workspace_size(const sssp_batch* b, const sssp_options* opt);
+
+/*
+ * Solve every problem of the batch in one persistent launch: blocks pull
+ * problems from a device work queue (largest graphs first) and each solves
+ * its problem alone -- init, Delta-ordered relaxation over the whole graph
+ * (one partition), unpack -- with no message traffic between blocks.
+ * Uploads the problem tables (host arrays) into ws on `stream` and waits for
+ * that copy, then launches.
+ */
+sssp_status sssp_solve_batched(const sssp_batch* b, const sssp_options* opt, void* ws, size_t ws_bytes,
+                               sssp_stream_t stream);
+
+/* A batched solve captured once into a CUDA graph and replayed. */
+typedef struct sssp_batch_plan sssp_batch_plan;
+
+/* Upload the tables, capture [counter reset, persistent kernel] into a CUDA
+ * graph on `stream` and instantiate it.  The plan keeps b's device pointers
+ * and ws; they must stay valid until sssp_batch_plan_destroy. Synchronous. */
+sssp_status sssp_batch_plan_create(const sssp_batch* b, const sssp_options* opt, void* ws, size_t ws_bytes,
+                                   sssp_stream_t stream, sssp_batch_plan** plan);
+/* Replay the captured graph on `stream` (asynchronous). */
+sssp_status sssp_batch_plan_launch(sssp_batch_plan* plan, sssp_stream_t stream);
+void sssp_batch_plan_destroy(sssp_batch_plan* plan);
+
+/* -------------------------------------------------------------- K6 backward */
+
+size_t sssp_backward_workspace_size(uint32_t V, uint32_t E, uint32_t S);
+
+/*
+ * Gradient of L = sum_s sum_v grad_dist[s][v] * dist_s(v) with respect to
+ * the edge weights (the paper has no gradients: dist_s(v) is the sum of the
+ * weights on the tree path to v, so dL/dw(e) sums grad_dist over the subtree
+ * below every tree edge e).  The upstream gradient is carried up each
+ * predecessor tree, children before parents (a reverse topological order of
+ * the tree, of which decreasing distance is one), accumulated in float64.
+ *   pred      : device [S][V] canonical predecessors from sssp_solve
+ *   grad_dist : device [S][V] float32 (values at unreachable vertices are ignored)
+ *   grad_w    : device [E] float32 out, CSR edge order, summed over the S sources;
+ *               non-tree edges get 0
+ */
+sssp_status sssp_backward(const sssp_graph* g, uint32_t S, const uint32_t* pred, const float* grad_dist,
+                          float* grad_w, void* ws, size_t ws_bytes, sssp_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SSSP_H */

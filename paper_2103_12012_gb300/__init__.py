@@ -1,0 +1,412 @@
+"""Python binding of libsssp, a GB300 (sm_103a) implementation of the hot path of
+SP_Async (arXiv 2103.12012): CSR build, 1D block partition, Trishla prune,
+asynchronous partitioned SSSP, batched SSSP and the tree backward.
+
+This module only marshals arguments: torch tensors provide device memory and
+the stream, every step runs in the CUDA kernels of ``_lib/libsssp.so`` behind
+the C ABI of ``include/sssp.h``.  There is no CPU fallback: if the library is
+missing or no GPU is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libsssp.so")
+_lib = None
+
+SSSP_OK, SSSP_EINVAL, SSSP_ENOMEM, SSSP_ECUDA, SSSP_ETIMEOUT, SSSP_EOVERFLOW, SSSP_EINTERNAL, SSSP_EUNSUPPORTED = \
+    range(8)
+W_U32, W_F32 = 0, 1
+FLAG_TEST_HOLD_PENDING = 0x1
+NONE = 0xFFFFFFFF
+
+P = ctypes.c_void_p
+u32, u64, i32, sz = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32, ctypes.c_size_t
+
+
+class SsspGraph(ctypes.Structure):
+    _fields_ = [("V", u32), ("E", u32), ("row_ptr", P), ("col", P), ("w", P), ("wtype", i32),
+                ("partitions", u32)]
+
+
+class SsspOptions(ctypes.Structure):
+    _fields_ = [("threads", u32), ("blocks_per_sm", u32), ("tile", u32), ("split", u32),
+                ("delta", ctypes.c_double), ("timeout_ns", u64), ("flags", u32), ("reserved", u32),
+                ("ev_relax_begin", P), ("ev_relax_end", P)]
+
+
+class SsspStats(ctypes.Structure):
+    _fields_ = [("edges_scanned", u64), ("atomics", u64), ("improved", u64), ("activations", u64),
+                ("rounds", u64), ("vertices", u64), ("remote_activations", u64), ("reserved", u64)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "reserved"}
+
+
+class SsspBatchGraph(ctypes.Structure):
+    _fields_ = [("row_off", u64), ("edge_off", u64), ("V", u32), ("E", u32)]
+
+
+class SsspBatch(ctypes.Structure):
+    _fields_ = [("n_graphs", u32), ("n_problems", u32), ("graphs", P), ("prob_graph", P), ("prob_source", P),
+                ("row_ptr", P), ("col", P), ("w", P), ("wtype", i32), ("dist", P), ("pred", P)]
+
+
+# name -> (restype, argtypes); the names are exactly the header's entry points
+_SIGS = {
+    "sssp_status_string": (ctypes.c_char_p, [i32]),
+    "sssp_version": (ctypes.c_char_p, []),
+    "sssp_build_csr_workspace_size": (sz, [u32, u64]),
+    "sssp_build_csr": (i32, [u32, u64, P, P, P, i32, P, P, P, P, P, P, sz, P]),
+    "sssp_partition": (i32, [P, P, P, P]),
+    "sssp_prune": (i32, [P, i32, P, P, P]),
+    "sssp_compact_workspace_size": (sz, [u32, u32]),
+    "sssp_compact": (i32, [P, P, P, P, P, P, P, P, sz, P]),
+    "sssp_solve_workspace_size": (sz, [P, u32, P]),
+    "sssp_solve": (i32, [P, P, u32, P, P, P, P, sz, P]),
+    "sssp_workspace_status": (i32, [P, P, P]),
+    "sssp_batch_workspace_size": (sz, [P, P]),
+    "sssp_solve_batched": (i32, [P, P, P, sz, P]),
+    "sssp_batch_plan_create": (i32, [P, P, P, sz, P, P]),
+    "sssp_batch_plan_launch": (i32, [P, P]),
+    "sssp_batch_plan_destroy": (None, [P]),
+    "sssp_backward_workspace_size": (sz, [u32, u32, u32]),
+    "sssp_backward": (i32, [P, u32, P, P, P, P, sz, P]),
+}
+
+
+class SsspError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} ({status})")
+
+
+def lib():
+    """The loaded libsssp (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libsssp is not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def status_string(s: int) -> str:
+    return lib().sssp_status_string(int(s)).decode()
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("libsssp needs a CUDA GPU")
+    return torch
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _check(st, where):
+    if st != SSSP_OK:
+        raise SsspError(st, where)
+
+
+def _ws(nbytes):
+    torch = _torch()
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device="cuda")
+
+
+def options(threads=0, blocks_per_sm=0, tile=0, split=0, delta=0.0, timeout_ns=0, flags=0) -> SsspOptions:
+    return SsspOptions(threads, blocks_per_sm, tile, split, float(delta), int(timeout_ns), flags, 0, None, None)
+
+
+@dataclass
+class DeviceGraph:
+    """A canonical CSR in device memory (torch int32 tensors holding uint32 values)."""
+    V: int
+    E: int
+    row_ptr: object
+    col: object
+    w: object  # int32 (uint32 bits) or float32
+    wtype: int
+    partitions: int = 1
+    eid: object = None  # kept edge -> index in the input edge list
+
+    def c(self) -> SsspGraph:
+        return SsspGraph(self.V, self.E, self.row_ptr.data_ptr(), self.col.data_ptr() if self.E else None,
+                         self.w.data_ptr() if self.E else None, self.wtype, self.partitions)
+
+    def with_partitions(self, P):
+        return DeviceGraph(self.V, self.E, self.row_ptr, self.col, self.w, self.wtype, P, self.eid)
+
+
+def _as_dev_u32(x):
+    torch = _torch()
+    if isinstance(x, np.ndarray):
+        x = torch.from_numpy(np.ascontiguousarray(x).view(np.int32))
+    return x.to("cuda", non_blocking=False).contiguous()
+
+
+def _w_dev(w):
+    torch = _torch()
+    if isinstance(w, np.ndarray):
+        if w.dtype == np.float32:
+            return torch.from_numpy(np.ascontiguousarray(w)).cuda(), W_F32
+        return torch.from_numpy(np.ascontiguousarray(w.astype(np.uint32)).view(np.int32)).cuda(), W_U32
+    return w.contiguous(), (W_F32 if w.dtype == torch.float32 else W_U32)
+
+
+def build_csr(V, src, dst, w, partitions=1, stream=None) -> DeviceGraph:
+    """K1: raw edge list -> canonical CSR (self-loops dropped, parallel edges collapsed to min weight)."""
+    torch = _torch()
+    src_d, dst_d = _as_dev_u32(src), _as_dev_u32(dst)
+    w_d, wt = _w_dev(w)
+    n = int(src_d.numel())
+    row_ptr = torch.empty(V + 1, dtype=torch.int32, device="cuda")
+    col = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
+    w_out = torch.empty(max(n, 1), dtype=w_d.dtype, device="cuda")
+    eid = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
+    E_out = torch.zeros(1, dtype=torch.int32, device="cuda")
+    L = lib()
+    nb = L.sssp_build_csr_workspace_size(V, n)
+    ws = _ws(nb)
+    st = _stream(stream)
+    _check(L.sssp_build_csr(V, n, _ptr(src_d), _ptr(dst_d), _ptr(w_d), wt, _ptr(row_ptr), _ptr(col), _ptr(w_out),
+                            _ptr(eid), _ptr(E_out), _ptr(ws), nb, st), "sssp_build_csr")
+    _check(L.sssp_workspace_status(_ptr(ws), st, None), "sssp_build_csr (device)")
+    E = int(E_out.item())
+    return DeviceGraph(V, E, row_ptr, col[:max(E, 1)], w_out[:max(E, 1)], wt, partitions, eid[:max(E, 1)])
+
+
+def upload_csr(V, row_ptr, col, w, partitions=1, eid=None) -> DeviceGraph:
+    """A CSR already in canonical form (e.g. from the oracle) copied to the device."""
+    w_d, wt = _w_dev(np.asarray(w))
+    E = int(np.asarray(row_ptr)[-1])
+    return DeviceGraph(V, E, _as_dev_u32(np.asarray(row_ptr, np.uint32)), _as_dev_u32(np.asarray(col, np.uint32)),
+                       w_d, wt, partitions, None if eid is None else _as_dev_u32(np.asarray(eid, np.uint32)))
+
+
+def partition(g: DeviceGraph, stream=None):
+    """K2: (bounds [P+1], inter-edges per partition [P]) as torch tensors."""
+    torch = _torch()
+    bounds = torch.empty(g.partitions + 1, dtype=torch.int32, device="cuda")
+    inter = torch.empty(g.partitions, dtype=torch.int64, device="cuda")
+    gc = g.c()
+    _check(lib().sssp_partition(ctypes.byref(gc), _ptr(bounds), _ptr(inter), _stream(stream)), "sssp_partition")
+    return bounds, inter
+
+
+def prune(g: DeviceGraph, mode=0, witness=True, stream=None):
+    """K3 Trishla: (keep uint8 [E], witness int32 [E] or None)."""
+    torch = _torch()
+    keep = torch.empty(max(g.E, 1), dtype=torch.uint8, device="cuda")
+    wit = torch.empty(max(g.E, 1), dtype=torch.int32, device="cuda") if witness else None
+    gc = g.c()
+    _check(lib().sssp_prune(ctypes.byref(gc), int(mode), _ptr(keep), _ptr(wit), _stream(stream)), "sssp_prune")
+    return keep[:g.E], (wit[:g.E] if wit is not None else None)
+
+
+def compact(g: DeviceGraph, keep, stream=None) -> DeviceGraph:
+    """The graph without the pruned edges; .eid maps kept edges to g's edge indices."""
+    torch = _torch()
+    row_ptr = torch.empty(g.V + 1, dtype=torch.int32, device="cuda")
+    col = torch.empty(max(g.E, 1), dtype=torch.int32, device="cuda")
+    w = torch.empty(max(g.E, 1), dtype=g.w.dtype, device="cuda")
+    emap = torch.empty(max(g.E, 1), dtype=torch.int32, device="cuda")
+    E_out = torch.zeros(1, dtype=torch.int32, device="cuda")
+    L = lib()
+    nb = L.sssp_compact_workspace_size(g.V, g.E)
+    ws = _ws(nb)
+    gc = g.c()
+    st = _stream(stream)
+    _check(L.sssp_compact(ctypes.byref(gc), _ptr(keep), _ptr(row_ptr), _ptr(col), _ptr(w), _ptr(emap), _ptr(E_out),
+                          _ptr(ws), nb, st), "sssp_compact")
+    E = int(E_out.item())
+    return DeviceGraph(g.V, E, row_ptr, col[:max(E, 1)], w[:max(E, 1)], g.wtype, g.partitions, emap[:max(E, 1)])
+
+
+class Solver:
+    """Reusable sssp_solve call: holds the workspace for (graph, S, options)."""
+
+    def __init__(self, g: DeviceGraph, S: int, opts: SsspOptions | None = None):
+        torch = _torch()
+        self.g, self.S = g, int(S)
+        self.opts = opts or options()
+        self.gc = g.c()
+        L = lib()
+        self.ws_bytes = L.sssp_solve_workspace_size(ctypes.byref(self.gc), self.S, ctypes.byref(self.opts))
+        if self.ws_bytes == 0:
+            raise SsspError(SSSP_EINVAL, "sssp_solve_workspace_size")
+        self.ws = _ws(self.ws_bytes)
+        dt = torch.float32 if g.wtype == W_F32 else torch.int32
+        self.dist = torch.empty((self.S, g.V), dtype=dt, device="cuda")
+        self.pred = torch.empty((self.S, g.V), dtype=torch.int32, device="cuda")
+
+    def launch(self, sources, dist=None, pred=None, stream=None):
+        """Asynchronous: enqueue the solve; returns the (dist, pred) tensors it writes."""
+        dist = self.dist if dist is None else dist
+        pred = self.pred if pred is None else pred
+        st = lib().sssp_solve(ctypes.byref(self.gc), _ptr(sources), self.S, _ptr(dist), _ptr(pred),
+                              ctypes.byref(self.opts), _ptr(self.ws), self.ws_bytes, _stream(stream))
+        _check(st, "sssp_solve")
+        return dist, pred
+
+    def status(self, stream=None):
+        stats = SsspStats()
+        st = lib().sssp_workspace_status(_ptr(self.ws), _stream(stream), ctypes.byref(stats))
+        return st, stats.as_dict()
+
+    def __call__(self, sources, check=True, stream=None):
+        torch = _torch()
+        if isinstance(sources, np.ndarray) or isinstance(sources, (list, tuple)):
+            sources = _as_dev_u32(np.asarray(sources, np.uint32))
+        dist, pred = self.launch(sources, stream=stream)
+        st, stats = self.status(stream)
+        if check and st not in (SSSP_OK,):
+            raise SsspError(st, "sssp_solve (device)")
+        self.last_status, self.last_stats = st, stats
+        return dist, pred
+
+
+def solve(g: DeviceGraph, sources, opts: SsspOptions | None = None, check=True):
+    """sssp_solve for the given sources; returns (dist [S,V], pred [S,V]) torch tensors."""
+    s = Solver(g, len(sources) if not hasattr(sources, "numel") else sources.numel(), opts)
+    d, p = s(sources, check=check)
+    return d.clone(), p.clone(), s.last_status, s.last_stats
+
+
+class Batch:
+    """A batch of independent (graph, source) problems over several graphs, solved in one launch."""
+
+    def __init__(self, graphs, sources, opts: SsspOptions | None = None):
+        """graphs: list of canonical oracle-style CSRs (objects with V, row_ptr, col, w numpy arrays);
+        sources: list of source arrays, one per graph."""
+        torch = _torch()
+        self.opts = opts or options()
+        Vs = [int(g.V) for g in graphs]
+        Es = [int(g.row_ptr[-1]) for g in graphs]
+        self.row_off = np.concatenate([[0], np.cumsum([v + 1 for v in Vs])[:-1]]).astype(np.uint64)
+        self.edge_off = np.concatenate([[0], np.cumsum(Es)[:-1]]).astype(np.uint64)
+        rp = np.concatenate([np.asarray(g.row_ptr, np.uint32) for g in graphs])
+        col = np.concatenate([np.asarray(g.col, np.uint32) for g in graphs])
+        wt = W_F32 if graphs[0].w.dtype == np.float32 else W_U32
+        w = np.concatenate([np.asarray(g.w) for g in graphs])
+        self.row_ptr = _as_dev_u32(rp)
+        self.col = _as_dev_u32(col)
+        self.w, self.wtype = _w_dev(w)
+        self.gdesc = (SsspBatchGraph * len(graphs))(*[SsspBatchGraph(int(a), int(b), v, e) for a, b, v, e in
+                                                      zip(self.row_off, self.edge_off, Vs, Es)])
+        pg, ps = [], []
+        for gi, s in enumerate(sources):
+            for x in np.asarray(s).tolist():
+                pg.append(gi)
+                ps.append(int(x))
+        self.prob_graph = np.asarray(pg, np.uint32)
+        self.prob_source = np.asarray(ps, np.uint32)
+        self.out_off = np.concatenate([[0], np.cumsum([Vs[g] for g in pg])[:-1]]).astype(np.int64)
+        self.Vs = Vs
+        total = int(sum(Vs[g] for g in pg))
+        dt = torch.float32 if wt == W_F32 else torch.int32
+        self.dist = torch.empty(total, dtype=dt, device="cuda")
+        self.pred = torch.empty(total, dtype=torch.int32, device="cuda")
+        self.c = SsspBatch(len(graphs), len(pg), ctypes.cast(self.gdesc, P), self.prob_graph.ctypes.data,
+                           self.prob_source.ctypes.data, self.row_ptr.data_ptr(), self.col.data_ptr(),
+                           self.w.data_ptr(), self.wtype, self.dist.data_ptr(), self.pred.data_ptr())
+        L = lib()
+        self.ws_bytes = L.sssp_batch_workspace_size(ctypes.byref(self.c), ctypes.byref(self.opts))
+        if self.ws_bytes == 0:
+            raise SsspError(SSSP_EINVAL, "sssp_batch_workspace_size")
+        self.ws = _ws(self.ws_bytes)
+        self.plan = None
+
+    @property
+    def n_problems(self):
+        return int(self.prob_graph.shape[0])
+
+    def solve(self, stream=None):
+        _check(lib().sssp_solve_batched(ctypes.byref(self.c), ctypes.byref(self.opts), _ptr(self.ws), self.ws_bytes,
+                                        _stream(stream)), "sssp_solve_batched")
+
+    def make_plan(self, stream=None):
+        h = ctypes.c_void_p()
+        _check(lib().sssp_batch_plan_create(ctypes.byref(self.c), ctypes.byref(self.opts), _ptr(self.ws),
+                                            self.ws_bytes, _stream(stream), ctypes.byref(h)), "sssp_batch_plan_create")
+        self.plan = h
+
+    def replay(self, stream=None):
+        _check(lib().sssp_batch_plan_launch(self.plan, _stream(stream)), "sssp_batch_plan_launch")
+
+    def status(self, stream=None):
+        stats = SsspStats()
+        st = lib().sssp_workspace_status(_ptr(self.ws), _stream(stream), ctypes.byref(stats))
+        return st, stats.as_dict()
+
+    def result(self, i):
+        """(dist, pred) views of problem i."""
+        o, v = int(self.out_off[i]), self.Vs[int(self.prob_graph[i])]
+        return self.dist[o:o + v], self.pred[o:o + v]
+
+    def __del__(self):
+        if getattr(self, "plan", None) is not None and _lib is not None:
+            _lib.sssp_batch_plan_destroy(self.plan)
+            self.plan = None
+
+
+def backward(g: DeviceGraph, pred, grad_dist, stream=None):
+    """K6: dL/dw (float32, CSR edge order) for L = sum grad_dist * dist."""
+    torch = _torch()
+    S = int(pred.shape[0])
+    grad_w = torch.empty(max(g.E, 1), dtype=torch.float32, device="cuda")
+    L = lib()
+    nb = L.sssp_backward_workspace_size(g.V, g.E, S)
+    ws = _ws(nb)
+    gc = g.c()
+    st = _stream(stream)
+    _check(L.sssp_backward(ctypes.byref(gc), S, _ptr(pred.contiguous()), _ptr(grad_dist.contiguous()), _ptr(grad_w),
+                           _ptr(ws), nb, st), "sssp_backward")
+    _check(L.sssp_workspace_status(_ptr(ws), st, None), "sssp_backward (device)")
+    return grad_w[:g.E]
+
+
+def _autograd():
+    torch = _torch()
+
+    class SSSPFunction(torch.autograd.Function):
+        """dist = SSSP(w) for fixed topology g and sources; differentiable in the float32 weights w."""
+
+        @staticmethod
+        def forward(ctx, w, g: DeviceGraph, sources, opts=None):
+            gw = DeviceGraph(g.V, g.E, g.row_ptr, g.col, w.detach().contiguous(), W_F32, g.partitions, g.eid)
+            solver = Solver(gw, int(sources.numel()), opts)
+            dist, pred = solver(sources)
+            ctx.g = gw
+            ctx.save_for_backward(pred)
+            return dist.clone()
+
+        @staticmethod
+        def backward(ctx, grad_dist):
+            (pred,) = ctx.saved_tensors
+            return backward(ctx.g, pred, grad_dist.float()), None, None, None
+
+    return SSSPFunction
+
+
+def sssp_function():
+    """torch.autograd.Function class for differentiable SSSP (created lazily so importing needs no GPU)."""
+    return _autograd()

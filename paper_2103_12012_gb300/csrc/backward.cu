@@ -1,0 +1,148 @@
+// K6 backward: dL/dw for L = sum_s sum_v g[s][v] * dist_s(v).
+//
+// dist_s(v) is the sum of the weights on the tree path from s to v, so
+// dL/dw(e) = sum over sources of the upstream gradient summed over the
+// subtree hanging below tree edge e.  The subtree sums are formed children
+// before parents without any sort or level loop: every vertex counts its
+// children; each leaf thread walks up its tree, adding its accumulated sum to
+// its tree edge and to its parent, then decrements the parent's child count;
+// only the thread that brings the count to zero continues upward (the
+// parent's sum is then complete), all others stop.  Each tree edge is
+// visited exactly once, so the work is O(S*V) plus the binary searches that
+// locate edge (pred(v), v) in pred(v)'s sorted row.  Accumulation is float64.
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace sssp {
+namespace {
+
+struct BwWs {
+    uint32_t* nchild;  // [S*V]
+    double* acc;       // [S*V]
+    double* grad;      // [E]
+    uint8_t* leaf;     // [S*V] snapshot of "has no children" taken before any walk starts
+    size_t total;
+};
+
+BwWs carve_bw(void* ws, uint32_t V, uint32_t E, uint32_t S) {
+    BwWs b{};
+    char* p = static_cast<char*>(ws);
+    size_t off = WS_HEADER_BYTES;
+    const size_t n = (size_t)S * V;
+    b.nchild = reinterpret_cast<uint32_t*>(p ? p + off : nullptr);
+    off += align_up(4 * std::max<size_t>(n, 1), 256);
+    b.acc = reinterpret_cast<double*>(p ? p + off : nullptr);
+    off += align_up(8 * std::max<size_t>(n, 1), 256);
+    b.grad = reinterpret_cast<double*>(p ? p + off : nullptr);
+    off += align_up(8 * std::max<size_t>(E, 1), 256);
+    b.leaf = reinterpret_cast<uint8_t*>(p ? p + off : nullptr);
+    off += align_up(std::max<size_t>(n, 1), 256);
+    b.total = off;
+    return b;
+}
+
+__device__ __forceinline__ int64_t find_edge(const uint32_t* row_ptr, const uint32_t* col, uint32_t a, uint32_t b) {
+    uint32_t lo = __ldg(&row_ptr[a]), hi = __ldg(&row_ptr[a + 1]);
+    const uint32_t end = hi;
+    while (lo < hi) {
+        const uint32_t m = lo + ((hi - lo) >> 1);
+        if (__ldg(&col[m]) < b)
+            lo = m + 1;
+        else
+            hi = m;
+    }
+    return (lo < end && __ldg(&col[lo]) == b) ? (int64_t)lo : -1;
+}
+
+__global__ void k_bw_init(size_t n, uint32_t E, const float* __restrict__ g, uint32_t* nchild, double* acc,
+                          double* grad) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        nchild[i] = 0u;
+        acc[i] = (double)g[i];
+    }
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < E; i += stride) grad[i] = 0.0;
+}
+
+__global__ void k_bw_count(uint32_t V, size_t n, const uint32_t* __restrict__ pred, uint32_t* nchild, WsHeader* hdr) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint32_t p = pred[i];
+        if (p == NONE) continue;
+        if (p >= V) {
+            set_status(hdr, SSSP_EINVAL);
+            continue;
+        }
+        atomicAdd(&nchild[i - (i % V) + p], 1u);
+    }
+}
+
+__global__ void k_bw_leaves(size_t n, const uint32_t* __restrict__ pred, const uint32_t* __restrict__ nchild,
+                            uint8_t* leaf) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        leaf[i] = (pred[i] != NONE && nchild[i] == 0u) ? 1u : 0u;
+}
+
+__global__ void k_bw_walk(uint32_t V, size_t n, const uint32_t* __restrict__ row_ptr, const uint32_t* __restrict__ col,
+                          const uint32_t* __restrict__ pred, const uint8_t* __restrict__ leaf, uint32_t* nchild,
+                          double* acc, double* grad, WsHeader* hdr) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        if (!leaf[i] || pred[i] >= V) continue;  // walks start at leaves only
+        const size_t base = i - (i % V);
+        uint32_t x = (uint32_t)(i - base);
+        // bounded by V steps: a tree path has fewer than V edges
+        for (uint32_t step = 0; step < V; ++step) {
+            const uint32_t p = __ldg(&pred[base + x]);
+            if (p == NONE) break;  // reached the source
+            const int64_t e = find_edge(row_ptr, col, p, x);
+            const double a = ld_relaxed(&acc[base + x]);
+            if (e < 0) {
+                set_status(hdr, SSSP_EINVAL);
+                break;
+            }
+            atomicAdd(&grad[e], a);
+            atomicAdd(&acc[base + p], a);
+            __threadfence();  // my contribution before my decrement
+            if (atomicSub(&nchild[base + p], 1u) != 1u) break;
+            __threadfence();  // every sibling's contribution before reading acc[p]
+            x = p;
+        }
+    }
+}
+
+__global__ void k_bw_out(uint32_t E, const double* __restrict__ grad, float* out) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < E; i += gridDim.x * blockDim.x)
+        out[i] = (float)grad[i];
+}
+
+unsigned grid_for(size_t n) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return (unsigned)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, (size_t)sms * 16));
+}
+
+}  // namespace
+
+size_t backward_workspace_bytes(uint32_t V, uint32_t E, uint32_t S) { return carve_bw(nullptr, V, E, S).total; }
+
+cudaError_t backward_launch(const sssp_graph* g, uint32_t S, const uint32_t* pred, const float* grad_dist,
+                            float* grad_w, void* ws, cudaStream_t st) {
+    BwWs b = carve_bw(ws, g->V, g->E, S);
+    WsHeader* hdr = static_cast<WsHeader*>(ws);
+    const size_t n = (size_t)S * g->V;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(hdr, 0, WS_HEADER_BYTES, st)) != cudaSuccess) return e;
+    k_bw_init<<<grid_for(std::max<size_t>(n, g->E)), 256, 0, st>>>(n, g->E, grad_dist, b.nchild, b.acc, b.grad);
+    k_bw_count<<<grid_for(n), 256, 0, st>>>(g->V, n, pred, b.nchild, hdr);
+    k_bw_leaves<<<grid_for(n), 256, 0, st>>>(n, pred, b.nchild, b.leaf);
+    k_bw_walk<<<grid_for(n), 256, 0, st>>>(g->V, n, g->row_ptr, g->col, pred, b.leaf, b.nchild, b.acc, b.grad, hdr);
+    k_bw_out<<<grid_for(g->E), 256, 0, st>>>(g->E, b.grad, grad_w);
+    return cudaGetLastError();
+}
+
+}  // namespace sssp

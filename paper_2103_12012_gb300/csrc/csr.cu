@@ -1,0 +1,264 @@
+// K1 CSR builder, K2 block partitioner, edge compaction.
+//
+// K1 turns a raw edge list into the canonical adjacency (Sec. III.A's Padj
+// for all partitions at once): keys (tail, head) are radix-sorted with their
+// input index (a stable sort, so equal keys keep input order), runs of equal
+// keys become one edge whose weight is the run's minimum (lowest input index
+// on ties, via a 64-bit atomicMin on (weight bits << 32 | index)), and
+// row_ptr is filled from the run boundaries.  Self-loops and bad ids sort to
+// the end behind a sentinel key and are dropped.  The radix sort and prefix
+// sums are CUB library primitives; the rest is hand-written here.
+#include <algorithm>
+#include <cub/device/device_radix_sort.cuh>
+#include <cub/device/device_scan.cuh>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace sssp {
+namespace {
+
+__host__ __device__ inline uint32_t bits_for(unsigned long long x) {
+    uint32_t b = 0;
+    while (b < 64 && (x >> b) != 0ull) ++b;
+    return b;
+}
+
+struct CsrWs {
+    WsHeader* hdr;
+    unsigned long long *keys_in, *keys_out;
+    uint32_t *vals_in, *vals_out;
+    uint32_t* runinc;             // [E_raw] inclusive run index
+    unsigned long long* runbest;  // [E_raw] (weight bits << 32 | input index)
+    void* cub_tmp;
+    size_t cub_bytes;
+    size_t total;
+};
+
+size_t cub_bytes_for(uint64_t n) {
+    size_t a = 0, b = 0;
+    cub::DeviceRadixSort::SortPairs(nullptr, a, (unsigned long long*)nullptr, (unsigned long long*)nullptr,
+                                    (uint32_t*)nullptr, (uint32_t*)nullptr, (int64_t)n, 0, 64);
+    cub::DeviceScan::InclusiveSum(nullptr, b, (uint32_t*)nullptr, (uint32_t*)nullptr, (int64_t)n);
+    return std::max(a, b);
+}
+
+CsrWs carve_csr(void* ws, uint32_t V, uint64_t n) {
+    (void)V;
+    CsrWs c{};
+    char* p = static_cast<char*>(ws);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        char* r = p ? p + off : nullptr;
+        off += align_up(bytes, 256);
+        return r;
+    };
+    c.hdr = reinterpret_cast<WsHeader*>(take(WS_HEADER_BYTES));
+    c.keys_in = reinterpret_cast<unsigned long long*>(take(8 * n));
+    c.keys_out = reinterpret_cast<unsigned long long*>(take(8 * n));
+    c.vals_in = reinterpret_cast<uint32_t*>(take(4 * n));
+    c.vals_out = reinterpret_cast<uint32_t*>(take(4 * n));
+    c.runinc = reinterpret_cast<uint32_t*>(take(4 * n));
+    c.runbest = reinterpret_cast<unsigned long long*>(take(8 * n));
+    c.cub_bytes = cub_bytes_for(n);
+    c.cub_tmp = take(c.cub_bytes);
+    c.total = off;
+    return c;
+}
+
+template <class W>
+__global__ void k_make_keys(uint32_t V, uint64_t n, const uint32_t* __restrict__ src, const uint32_t* __restrict__ dst,
+                            const uint32_t* __restrict__ w, unsigned long long* keys, uint32_t* vals, WsHeader* hdr) {
+    const unsigned long long sentinel = (unsigned long long)V * V;
+    bool bad = false;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t s = src[i], d = dst[i];
+        unsigned long long k = sentinel;
+        if (s >= V || d >= V || !W::weight_ok(w[i]))
+            bad = true;
+        else if (s != d)
+            k = (unsigned long long)s * V + d;
+        keys[i] = k;
+        vals[i] = (uint32_t)i;
+    }
+    if (bad) set_status(hdr, SSSP_EINVAL);
+}
+
+// run head flag: first element of a run of equal valid keys
+__global__ void k_heads(uint64_t n, unsigned long long sentinel, const unsigned long long* __restrict__ keys,
+                        uint32_t* heads) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const unsigned long long k = keys[i];
+        heads[i] = (k != sentinel && (i == 0 || keys[i - 1] != k)) ? 1u : 0u;
+    }
+}
+
+__global__ void k_run_min(uint64_t n, unsigned long long sentinel, const unsigned long long* __restrict__ keys,
+                          const uint32_t* __restrict__ vals, const uint32_t* __restrict__ w,
+                          const uint32_t* __restrict__ runinc, unsigned long long* runbest) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        if (keys[i] == sentinel) continue;
+        const uint32_t id = vals[i];
+        atomicMin(&runbest[runinc[i] - 1u], ((unsigned long long)w[id] << 32) | id);
+    }
+}
+
+// one thread per run head: emit the edge and the row_ptr entries up to its tail
+__global__ void k_emit(uint32_t V, uint64_t n, unsigned long long sentinel, const unsigned long long* __restrict__ keys,
+                       const uint32_t* __restrict__ runinc, const unsigned long long* __restrict__ runbest,
+                       uint32_t* row_ptr, uint32_t* col, uint32_t* w_out, uint32_t* eid, uint32_t* E_out) {
+    const uint32_t R = n ? runinc[n - 1] : 0u;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const unsigned long long k = keys[i];
+        if (k == sentinel || (i > 0 && keys[i - 1] == k)) continue;
+        const uint32_t r = runinc[i] - 1u;
+        const uint32_t s = (uint32_t)(k / V), d = (uint32_t)(k % V);
+        const unsigned long long best = runbest[r];
+        col[r] = d;
+        w_out[r] = (uint32_t)(best >> 32);
+        if (eid) eid[r] = (uint32_t)best;
+        // rows (s_prev, s] start at r
+        const uint32_t s_prev = (r == 0) ? 0u : (uint32_t)(keys[i - 1] / V) + 1u;
+        for (uint32_t u = (r == 0 ? 0u : s_prev); u <= s; ++u) row_ptr[u] = r;
+        if (r + 1u == R)
+            for (uint32_t u = s + 1u; u <= V; ++u) row_ptr[u] = R;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *E_out = R;
+        if (R == 0)
+            for (uint32_t u = 0; u <= V; ++u) row_ptr[u] = 0;
+    }
+}
+
+__global__ void k_partition(uint32_t V, uint32_t P, unsigned long long B, const uint32_t* __restrict__ row_ptr,
+                            const uint32_t* __restrict__ col, uint32_t* bounds, unsigned long long* inter) {
+    const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t p = gtid; p <= P; p += stride)
+        bounds[p] = (uint32_t)std::min<unsigned long long>((unsigned long long)p * B, V);
+    if (!inter) return;
+    for (uint32_t u = gtid; u < V; u += stride) {
+        const uint32_t pu = (uint32_t)(u / B);
+        uint32_t c = 0;
+        const uint32_t e1 = row_ptr[u + 1];
+        for (uint32_t e = row_ptr[u]; e < e1; ++e) c += (uint32_t)(col[e] / B) != pu;
+        if (c) atomicAdd(&inter[pu], (unsigned long long)c);
+    }
+}
+
+__global__ void k_keep_u32(uint32_t E, const uint8_t* __restrict__ keep, uint32_t* out) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < E; i += gridDim.x * blockDim.x)
+        out[i] = keep[i] ? 1u : 0u;
+}
+
+// pos = inclusive scan of keep
+__global__ void k_compact(uint32_t V, uint32_t E, const uint32_t* __restrict__ row_ptr, const uint32_t* __restrict__ col,
+                          const uint32_t* __restrict__ w, const uint8_t* __restrict__ keep,
+                          const uint32_t* __restrict__ pos, uint32_t* row_ptr_out, uint32_t* col_out,
+                          uint32_t* w_out, uint32_t* emap, uint32_t* E_out) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    for (uint32_t i = gtid; i < E; i += stride) {
+        if (!keep[i]) continue;
+        const uint32_t j = pos[i] - 1u;
+        col_out[j] = col[i];
+        w_out[j] = w[i];
+        if (emap) emap[j] = i;
+    }
+    for (uint32_t u = gtid; u <= V; u += stride) {
+        const uint32_t r = row_ptr[u];
+        row_ptr_out[u] = r == 0 ? 0u : pos[r - 1];
+    }
+    if (gtid == 0) *E_out = E ? pos[E - 1] : 0u;
+}
+
+unsigned grid_for(uint64_t n, unsigned threads = 256) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const uint64_t want = (n + threads - 1) / threads;
+    return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)sms * 16));
+}
+
+}  // namespace
+
+size_t csr_workspace_bytes(uint32_t V, uint64_t E_raw) { return carve_csr(nullptr, V, E_raw).total; }
+
+#define CK(x)                                        \
+    do {                                             \
+        if ((x) != cudaSuccess) return SSSP_ECUDA;   \
+    } while (0)
+
+sssp_status csr_build(uint32_t V, uint64_t n, const uint32_t* src, const uint32_t* dst, const uint32_t* w, int wtype,
+                      uint32_t* row_ptr, uint32_t* col, uint32_t* w_out, uint32_t* eid, uint32_t* E_out, void* ws,
+                      size_t ws_bytes, cudaStream_t st) {
+    CsrWs c = carve_csr(ws, V, n);
+    if (ws_bytes < c.total) return SSSP_ENOMEM;
+    const unsigned long long sentinel = (unsigned long long)V * V;
+    const int end_bit = (int)bits_for(sentinel);
+    CK(cudaMemsetAsync(c.hdr, 0, WS_HEADER_BYTES, st));
+    CK(cudaMemsetAsync(row_ptr, 0, sizeof(uint32_t) * ((size_t)V + 1), st));
+    CK(cudaMemsetAsync(E_out, 0, sizeof(uint32_t), st));
+    if (n == 0) return SSSP_OK;
+    const unsigned g = grid_for(n);
+    if (wtype == SSSP_W_F32)
+        k_make_keys<WF32><<<g, 256, 0, st>>>(V, n, src, dst, w, c.keys_in, c.vals_in, c.hdr);
+    else
+        k_make_keys<WU32><<<g, 256, 0, st>>>(V, n, src, dst, w, c.keys_in, c.vals_in, c.hdr);
+    CK(cudaGetLastError());
+    size_t tb = c.cub_bytes;
+    CK(cub::DeviceRadixSort::SortPairs(c.cub_tmp, tb, c.keys_in, c.keys_out, c.vals_in, c.vals_out, (int64_t)n, 0,
+                                       end_bit, st));
+    k_heads<<<g, 256, 0, st>>>(n, sentinel, c.keys_out, c.vals_in);  // vals_in reused as head flags
+    CK(cudaGetLastError());
+    tb = c.cub_bytes;
+    CK(cub::DeviceScan::InclusiveSum(c.cub_tmp, tb, c.vals_in, c.runinc, (int64_t)n, st));
+    CK(cudaMemsetAsync(c.runbest, 0xFF, 8 * n, st));
+    k_run_min<<<g, 256, 0, st>>>(n, sentinel, c.keys_out, c.vals_out, w, c.runinc, c.runbest);
+    CK(cudaGetLastError());
+    k_emit<<<g, 256, 0, st>>>(V, n, sentinel, c.keys_out, c.runinc, c.runbest, row_ptr, col, w_out, eid, E_out);
+    CK(cudaGetLastError());
+    return SSSP_OK;
+}
+
+cudaError_t partition_launch(const sssp_graph* g, uint32_t* bounds, uint64_t* inter, cudaStream_t st) {
+    const unsigned long long B = ((unsigned long long)g->V + g->partitions - 1) / g->partitions;
+    cudaError_t e;
+    if (inter && (e = cudaMemsetAsync(inter, 0, sizeof(uint64_t) * g->partitions, st)) != cudaSuccess) return e;
+    k_partition<<<grid_for(std::max<uint64_t>(g->V, g->partitions + 1)), 256, 0, st>>>(
+        g->V, g->partitions, B, g->row_ptr, g->col, bounds, reinterpret_cast<unsigned long long*>(inter));
+    return cudaGetLastError();
+}
+
+size_t compact_workspace_bytes(uint32_t V, uint32_t E) {
+    (void)V;
+    size_t a = 0;
+    cub::DeviceScan::InclusiveSum(nullptr, a, (uint32_t*)nullptr, (uint32_t*)nullptr, (int64_t)E);
+    return WS_HEADER_BYTES + 2 * align_up(4ull * std::max<uint32_t>(E, 1), 256) + align_up(a, 256);
+}
+
+sssp_status compact_launch(const sssp_graph* g, const uint8_t* keep, uint32_t* row_ptr_out, uint32_t* col_out,
+                           uint32_t* w_out, uint32_t* emap_out, uint32_t* E_out, void* ws, size_t ws_bytes,
+                           cudaStream_t st) {
+    if (ws_bytes < compact_workspace_bytes(g->V, g->E)) return SSSP_ENOMEM;
+    char* p = static_cast<char*>(ws);
+    WsHeader* hdr = reinterpret_cast<WsHeader*>(p);
+    uint32_t* flags = reinterpret_cast<uint32_t*>(p + WS_HEADER_BYTES);
+    uint32_t* pos = reinterpret_cast<uint32_t*>(p + WS_HEADER_BYTES + align_up(4ull * std::max<uint32_t>(g->E, 1), 256));
+    void* tmp = p + WS_HEADER_BYTES + 2 * align_up(4ull * std::max<uint32_t>(g->E, 1), 256);
+    CK(cudaMemsetAsync(hdr, 0, WS_HEADER_BYTES, st));
+    const unsigned gr = grid_for(std::max<uint64_t>(g->E, (uint64_t)g->V + 1));
+    if (g->E) {
+        k_keep_u32<<<gr, 256, 0, st>>>(g->E, keep, flags);
+        CK(cudaGetLastError());
+        size_t tb = 0;
+        cub::DeviceScan::InclusiveSum(nullptr, tb, flags, pos, (int64_t)g->E, st);
+        CK(cub::DeviceScan::InclusiveSum(tmp, tb, flags, pos, (int64_t)g->E, st));
+    }
+    k_compact<<<gr, 256, 0, st>>>(g->V, g->E, g->row_ptr, g->col, static_cast<const uint32_t*>(g->w), keep, pos,
+                                  row_ptr_out, col_out, w_out, emap_out, E_out);
+    CK(cudaGetLastError());
+    return SSSP_OK;
+}
+
+}  // namespace sssp

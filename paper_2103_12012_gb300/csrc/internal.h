@@ -1,0 +1,102 @@
+// Host-side interfaces between the C-ABI layer (api.cu) and the kernel files.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "sssp.h"
+
+namespace sssp {
+
+struct WsHeader;
+
+// ------------------------------------------------------------------ relax.cu
+struct SolveLaunch {
+    // graph
+    const uint32_t* row_ptr;
+    const uint32_t* col;
+    const uint32_t* w;
+    int wtype;
+    uint32_t V;
+    // problems
+    uint32_t S;
+    const uint32_t* sources;
+    // ownership
+    uint32_t B;      // partition block size ceil(V/P)
+    uint32_t Bq;     // sub-block size ceil(B/split)
+    uint32_t split;  // sub-blocks per partition
+    uint32_t Q;      // units per source = P*split
+    uint32_t words;  // bitmap words per source
+    // workspace views
+    WsHeader* hdr;
+    unsigned long long* packed;  // [S][V]
+    uint32_t* bitmap;            // [S][words]
+    uint32_t* dirty;             // [S*Q]
+    // schedule
+    uint32_t threads, tile, grid;
+    uint32_t delta_bits;
+    uint64_t timeout_ns;
+    uint32_t hold_pending;
+    cudaEvent_t ev_begin, ev_end;  // optional timing events around the relaxation kernel
+    // outputs
+    uint32_t* dist;
+    uint32_t* pred;
+};
+
+size_t relax_smem_bytes(uint32_t tile, uint32_t Q);
+cudaError_t relax_max_blocks_per_sm(int wtype, uint32_t threads, uint32_t tile, uint32_t Q, int* out);
+cudaError_t launch_solve(const SolveLaunch& L, cudaStream_t st);
+
+// One problem of a batch, in the order blocks take them (largest first).
+struct BatchProblem {
+    unsigned long long row_off, edge_off, out_off, bm_off;
+    uint32_t V, src, E, pad;
+};
+static_assert(sizeof(BatchProblem) == 48, "batch problem layout");
+
+struct BatchLaunch {
+    const uint32_t* row_ptr;
+    const uint32_t* col;
+    const uint32_t* w;
+    int wtype;
+    uint32_t n_problems;
+    const BatchProblem* probs;  // device
+    WsHeader* hdr;
+    unsigned long long* packed;  // [sum V]
+    uint32_t* bitmap;
+    uint32_t threads, tile, grid;
+    uint32_t delta_bits;
+    uint64_t timeout_ns;
+    uint32_t* dist;
+    uint32_t* pred;
+    cudaEvent_t ev_begin, ev_end;
+};
+
+cudaError_t batched_max_blocks_per_sm(int wtype, uint32_t threads, uint32_t tile, int* out);
+cudaError_t launch_batched(const BatchLaunch& L, cudaStream_t st);
+
+// -------------------------------------------------------------------- csr.cu
+size_t csr_workspace_bytes(uint32_t V, uint64_t E_raw);
+sssp_status csr_build(uint32_t V, uint64_t E_raw, const uint32_t* src, const uint32_t* dst, const uint32_t* w,
+                      int wtype, uint32_t* row_ptr, uint32_t* col, uint32_t* w_out, uint32_t* eid, uint32_t* E_out,
+                      void* ws, size_t ws_bytes, cudaStream_t st);
+cudaError_t partition_launch(const sssp_graph* g, uint32_t* bounds, uint64_t* inter, cudaStream_t st);
+size_t compact_workspace_bytes(uint32_t V, uint32_t E);
+sssp_status compact_launch(const sssp_graph* g, const uint8_t* keep, uint32_t* row_ptr_out, uint32_t* col_out,
+                           uint32_t* w_out, uint32_t* emap_out, uint32_t* E_out, void* ws, size_t ws_bytes,
+                           cudaStream_t st);
+
+// ------------------------------------------------------------------ prune.cu
+cudaError_t prune_launch(const sssp_graph* g, int mode, uint8_t* keep, uint32_t* witness, cudaStream_t st);
+
+// --------------------------------------------------------------- backward.cu
+size_t backward_workspace_bytes(uint32_t V, uint32_t E, uint32_t S);
+cudaError_t backward_launch(const sssp_graph* g, uint32_t S, const uint32_t* pred, const float* grad_dist,
+                            float* grad_w, void* ws, cudaStream_t st);
+
+// ------------------------------------------------------------------- common
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+constexpr size_t WS_HEADER_BYTES = 256;
+
+}  // namespace sssp

@@ -1,0 +1,678 @@
+// K0 init / K4 persistent relaxation / K5 batched relaxation / unpack.
+//
+// The SP-Async loop of Sec. III.C on one GPU.  Vertices are split into
+// units: a unit is one sub-block of one partition (Sec. III.A 1D block
+// partitioning, sub-divided `split` ways) for one source.  Each unit has one
+// owner thread block.  Per source the device state is
+//   packed[v] : 64-bit word (dist << 32 | pred), lowered only by atomicMin;
+//               dist is the uint32 distance or the bits of a non-negative
+//               float32 distance, whose unsigned order is the numeric order.
+//   bitmap[v] : 1 bit per vertex, the inbox: set when v's distance dropped
+//               and v must be (re)processed (Alg. 2 pq.push / Alg. 3 push or
+//               send_msg), cleared by the owner when it takes v.
+//   dirty[q]  : a unit's doorbell, rung after new bits land in its range.
+// A round of a unit (Alg. 2 recv_msgs + DIJKSTRA, bucketed):
+//   A  scan the unit's inbox words, read each queued vertex's distance, and
+//      find the minimum dmin;
+//   B  select the queued vertices with dist < dmin + delta (the near bucket,
+//      an approximation of Dijkstra's pop order inside the partition), at
+//      most `tile` of them;
+//   C  take them: clear their inbox bits (acquire);
+//   D  re-read their distances and CSR row extents; prefix-sum the degrees;
+//   E  relax every out-edge of the taken vertices with the whole block in
+//      edge-parallel, coalesced order: cand = d(u)+w(u,v); if the packed key
+//      (cand, u) is below the target's word, atomicMin it; if that lowered
+//      the distance, set v's inbox bit (release) -- a local push when v is
+//      in this unit, a message (Alg. 3 send_msg) otherwise;
+//   F  settle the termination count and ring the doorbells of every unit
+//      that received a new vertex.
+// Termination (Sec. III.D, the message counter of ToKa): `pending` counts
+// queued vertices plus vertices taken but not yet finished.  A round first
+// reserves one count per edge it will relax (so a vertex is counted before
+// its bit is visible), then returns the unused reservations and its taken
+// vertices.  pending == 0 therefore means no queued and no in-flight work
+// anywhere, and it can never rise again; every block then exits.  Every wait
+// is bounded by a %globaltimer limit after which the block records
+// SSSP_ETIMEOUT, raises the abort flag and returns.
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace sssp {
+namespace {
+
+constexpr unsigned long long SRC_KEY = 0x00000000FFFFFFFFull;  // dist 0, pred NONE
+constexpr uint64_t KERNEL_LIMIT_FACTOR = 3;  // whole-kernel wall-clock limit = 3 x idle limit
+
+__device__ __forceinline__ uint32_t atom_or_release(uint32_t* p, uint32_t v) {
+    uint32_t old;
+    asm volatile("atom.release.gpu.global.or.b32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+__device__ __forceinline__ uint32_t atom_and_acquire(uint32_t* p, uint32_t v) {
+    uint32_t old;
+    asm volatile("atom.acquire.gpu.global.and.b32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+__device__ __forceinline__ uint32_t warp_min(uint32_t x) {
+    for (int o = 16; o > 0; o >>= 1) x = min(x, __shfl_xor_sync(0xFFFFFFFFu, x, o));
+    return x;
+}
+
+__device__ __forceinline__ uint32_t warp_sum(uint32_t x) {
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
+    return x;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum64(unsigned long long x) {
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
+    return x;
+}
+
+// bits of inbox word `wd` that belong to vertices in [lo, hi)
+__device__ __forceinline__ uint32_t range_mask(uint32_t wd, uint32_t lo, uint32_t hi) {
+    const uint32_t base = wd * 32u;
+    uint32_t m = 0xFFFFFFFFu;
+    if (base < lo) m &= 0xFFFFFFFFu << (lo - base);
+    if (base + 32u > hi) m &= 0xFFFFFFFFu >> (base + 32u - hi);
+    return m;
+}
+
+// In-place exclusive scan of a[0..n) in shared memory by the whole block;
+// returns the total.  wsum: 32 words of shared scratch.
+__device__ uint32_t block_scan_excl(uint32_t* a, uint32_t n, uint32_t* wsum) {
+    const uint32_t T = blockDim.x, tid = threadIdx.x, lane = tid & 31u, wid = tid >> 5, nw = T >> 5;
+    const uint32_t chunk = (n + T - 1u) / T;
+    const uint32_t beg = min(tid * chunk, n), end = min(beg + chunk, n);
+    uint32_t s = 0;
+    for (uint32_t i = beg; i < end; ++i) s += a[i];
+    uint32_t x = s;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if ((int)lane >= o) x += y;
+    }
+    if (lane == 31u) wsum[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t t = lane < nw ? wsum[lane] : 0u;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xFFFFFFFFu, t, o);
+            if ((int)lane >= o) t += y;
+        }
+        if (lane < nw) wsum[lane] = t;
+    }
+    __syncthreads();
+    uint32_t base = (wid ? wsum[wid - 1] : 0u) + x - s;
+    for (uint32_t i = beg; i < end; ++i) {
+        uint32_t v = a[i];
+        a[i] = base;
+        base += v;
+    }
+    const uint32_t total = wsum[nw - 1];
+    __syncthreads();
+    return total;
+}
+
+// Bucket bound for a round: dmin + delta, at least one step above dmin,
+// saturating to "everything finite".
+template <class W>
+__device__ __forceinline__ uint32_t bucket_bound(uint32_t dmin, uint32_t delta) {
+    uint32_t t;
+    if (!W::add(dmin, delta, t)) return 0xFFFFFFFFu;
+    return t > dmin ? t : dmin + 1u;
+}
+
+struct Scalars {
+    uint32_t cnt, nlist, dmin, nsel, nclaim, act, bad;
+    int pick;
+    unsigned long long prob;
+};
+
+struct Counters {
+    unsigned long long edges, atomics, improved, acts, rounds, verts, remote;
+};
+
+// Per-round view of one problem (one source on one graph).
+struct Ctx {
+    const uint32_t* row_ptr;
+    const uint32_t* col;
+    const uint32_t* w;
+    uint32_t V;
+    unsigned long long* packed;
+    uint32_t* bitmap;
+    WsHeader* hdr;
+    uint32_t delta, tile;
+    // static-ownership mode only
+    uint32_t* dirty;  // this source's unit doorbells
+    uint32_t B, Bq, split, Qw;
+};
+
+struct Smem {
+    uint32_t* list_v;   // [tile]  A: queued ids;       D/E: row start of taken vertex
+    uint32_t* list_d;   // [tile]  A: queued distances; D/E: distance of taken vertex
+    uint32_t* sel_v;    // [tile]  taken vertex ids
+    uint32_t* sel_pref; // [tile+1] degree prefix sums
+    uint32_t* touched;  // [Qw] units that got a new queued vertex this round (static mode)
+    uint32_t* wsum;     // [32]
+    Scalars* sc;
+};
+
+// One round over the unit owning vertices [lo, hi).  Returns the number of
+// queued vertices the scan found (0 = the unit's inbox was empty).
+template <class W, bool STATIC>
+__device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t my_q, const Smem& sm,
+                                Counters& cnt) {
+    const uint32_t T = blockDim.x, tid = threadIdx.x, lane = tid & 31u;
+    Scalars& sc = *sm.sc;
+    if (tid == 0) {
+        sc.cnt = 0;
+        sc.nlist = 0;
+        sc.dmin = 0xFFFFFFFFu;
+        sc.nsel = 0;
+        sc.nclaim = 0;
+        sc.act = 0;
+        sc.bad = 0;
+    }
+    __syncthreads();
+
+    // ---- A: scan the inbox, gather queued vertices and their distances
+    const uint32_t wlo = lo >> 5, whi = (hi - 1u) >> 5;
+    uint32_t lmin = 0xFFFFFFFFu, lcnt = 0;
+    for (uint32_t wd = wlo + tid; wd <= whi; wd += T) {
+        uint32_t bits = ld_relaxed(&c.bitmap[wd]) & range_mask(wd, lo, hi);
+        while (bits) {
+            const uint32_t b = __ffs(bits) - 1u;
+            bits &= bits - 1u;
+            const uint32_t v = wd * 32u + b;
+            const uint32_t d = (uint32_t)(ld_relaxed(&c.packed[v]) >> 32);
+            lmin = min(lmin, d);
+            ++lcnt;
+            const uint32_t idx = atomicAdd(&sc.nlist, 1u);
+            if (idx < c.tile) {
+                sm.list_v[idx] = v;
+                sm.list_d[idx] = d;
+            }
+        }
+    }
+    lmin = warp_min(lmin);
+    lcnt = warp_sum(lcnt);
+    if (lane == 0 && lcnt) {
+        atomicMin(&sc.dmin, lmin);
+        atomicAdd(&sc.cnt, lcnt);
+    }
+    __syncthreads();
+    const uint32_t found = sc.cnt;
+    if (found == 0) return 0;
+    const uint32_t thr = bucket_bound<W>(sc.dmin, c.delta);
+
+    // ---- B: the near bucket, at most `tile` vertices
+    if (found <= c.tile) {
+        for (uint32_t i = tid; i < found; i += T)
+            if (sm.list_d[i] < thr) sm.sel_v[atomicAdd(&sc.nsel, 1u)] = sm.list_v[i];
+    } else {
+        for (uint32_t wd = wlo + tid; wd <= whi; wd += T) {
+            uint32_t bits = ld_relaxed(&c.bitmap[wd]) & range_mask(wd, lo, hi);
+            while (bits) {
+                const uint32_t b = __ffs(bits) - 1u;
+                bits &= bits - 1u;
+                const uint32_t v = wd * 32u + b;
+                if ((uint32_t)(ld_relaxed(&c.packed[v]) >> 32) < thr) {
+                    const uint32_t j = atomicAdd(&sc.nsel, 1u);
+                    if (j < c.tile) sm.sel_v[j] = v;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const uint32_t nsel = min(sc.nsel, c.tile);
+
+    // ---- C: take them off the inbox
+    uint32_t myclaim = 0;
+    for (uint32_t i = tid; i < nsel; i += T) {
+        const uint32_t v = sm.sel_v[i], bit = 1u << (v & 31u);
+        const uint32_t old = atom_and_acquire(&c.bitmap[v >> 5], ~bit);
+        if (old & bit)
+            ++myclaim;
+        else
+            sm.sel_v[i] = NONE;
+    }
+    // ---- D: distances and row extents of the taken vertices (same thread as its take)
+    for (uint32_t i = tid; i < nsel; i += T) {
+        const uint32_t u = sm.sel_v[i];
+        uint32_t deg = 0, beg = 0, du = 0;
+        if (u != NONE) {
+            du = (uint32_t)(ld_relaxed(&c.packed[u]) >> 32);
+            beg = __ldg(&c.row_ptr[u]);
+            deg = __ldg(&c.row_ptr[u + 1]) - beg;
+        }
+        sm.list_d[i] = du;
+        sm.list_v[i] = beg;
+        sm.sel_pref[i] = deg;
+    }
+    myclaim = warp_sum(myclaim);
+    if (lane == 0 && myclaim) atomicAdd(&sc.nclaim, myclaim);
+    __syncthreads();
+    const uint32_t te = block_scan_excl(sm.sel_pref, nsel, sm.wsum);
+    if (tid == 0) sm.sel_pref[nsel] = te;
+    if (STATIC) {
+        // reserve one termination count per edge before any new bit can be seen
+        if (tid == 0 && te) {
+            atomicAdd(&c.hdr->pending, (unsigned long long)te);
+            __threadfence();
+        }
+    }
+    __syncthreads();
+
+    // ---- E: relax all out-edges, edge-parallel
+    uint32_t lact = 0, bad = 0;
+    for (uint32_t k = tid; k < te; k += T) {
+        uint32_t a = 0, b = nsel;  // sel_pref[a] <= k < sel_pref[b]
+        while (b - a > 1u) {
+            const uint32_t m = (a + b) >> 1;
+            if (sm.sel_pref[m] <= k)
+                a = m;
+            else
+                b = m;
+        }
+        const uint32_t e = sm.list_v[a] + (k - sm.sel_pref[a]);
+        const uint32_t u = sm.sel_v[a], du = sm.list_d[a];
+        const uint32_t v = __ldg(&c.col[e]);
+        const uint32_t wt = __ldg(&c.w[e]);
+        if (!W::weight_ok(wt) || v >= c.V) {
+            bad |= 1u;
+            continue;
+        }
+        uint32_t cand;
+        if (!W::add(du, wt, cand)) {
+            bad |= 2u;
+            continue;
+        }
+        const unsigned long long key = ((unsigned long long)cand << 32) | u;
+        if (key < ld_relaxed(&c.packed[v])) {
+            ++cnt.atomics;
+            const unsigned long long old = atomicMin(&c.packed[v], key);
+            if (key < old && (uint32_t)(old >> 32) > cand) {
+                ++cnt.improved;
+                const uint32_t bit = 1u << (v & 31u);
+                const uint32_t ob = atom_or_release(&c.bitmap[v >> 5], bit);
+                if (!(ob & bit)) {
+                    ++lact;
+                    if (STATIC) {
+                        const uint32_t p = v / c.B;
+                        const uint32_t q = p * c.split + (v - p * c.B) / c.Bq;
+                        if (q != my_q) ++cnt.remote;
+                        atomicOr(&sm.touched[q >> 5], 1u << (q & 31u));
+                    }
+                }
+            }
+        }
+    }
+    lact = warp_sum(lact);
+    bad = __reduce_or_sync(0xFFFFFFFFu, bad);
+    if (lane == 0) {
+        if (lact) atomicAdd(&sc.act, lact);
+        if (bad) atomicOr(&sc.bad, bad);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        cnt.edges += te;
+        cnt.rounds += 1;
+        cnt.verts += sc.nclaim;
+        cnt.acts += sc.act;
+        if (sc.bad & 1u) set_status(c.hdr, SSSP_EINVAL);
+        if (sc.bad & 2u) set_status(c.hdr, SSSP_EOVERFLOW);
+    }
+
+    // ---- F: settle the count, ring doorbells
+    if (STATIC) {
+        if (tid == 0) {
+            const long long d = (long long)sc.act - (long long)te - (long long)sc.nclaim;
+            if (d) atomicAdd(&c.hdr->pending, (unsigned long long)d);
+        }
+        __threadfence();  // new bits (set before the barrier above) before the doorbells
+        for (uint32_t wq = tid; wq < c.Qw; wq += T) {
+            uint32_t bits = sm.touched[wq];
+            if (!bits) continue;
+            sm.touched[wq] = 0;
+            while (bits) {
+                const uint32_t b = __ffs(bits) - 1u;
+                bits &= bits - 1u;
+                st_relaxed(&c.dirty[wq * 32u + b], 1u);
+            }
+        }
+        if (tid == 0 && found > sc.nclaim) st_relaxed(&c.dirty[my_q], 1u);  // more left in this unit
+    }
+    __syncthreads();
+    return found;
+}
+
+__device__ Smem carve(uint32_t* dsm, uint32_t tile, uint32_t Qw, uint32_t* wsum, Scalars* sc) {
+    Smem s;
+    s.list_v = dsm;
+    s.list_d = dsm + tile;
+    s.sel_v = dsm + 2 * tile;
+    s.sel_pref = dsm + 3 * tile;
+    s.touched = dsm + 4 * tile + 1;
+    s.wsum = wsum;
+    s.sc = sc;
+    (void)Qw;
+    return s;
+}
+
+__device__ void flush_counters(WsHeader* h, const Counters& c) {
+    // counters accumulated per thread (atomics/improved/remote) or by thread 0 (the rest)
+    // stats order follows sssp_stats
+    const unsigned long long v[7] = {c.edges, c.atomics, c.improved, c.acts, c.rounds, c.verts, c.remote};
+#pragma unroll
+    for (int i = 0; i < 7; ++i) {
+        const unsigned long long x = warp_sum64(v[i]);
+        if ((threadIdx.x & 31u) == 0 && x) atomicAdd(&h->stats[i], x);
+    }
+}
+
+// ---------------------------------------------------------------- kernels
+
+// K0: every packed word to INF, inboxes and doorbells to zero.
+__global__ void k_init_fill(unsigned long long* packed, size_t n_packed, uint32_t* bitmap, size_t n_words,
+                            uint32_t* dirty, size_t n_dirty) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    ulonglong2* p2 = reinterpret_cast<ulonglong2*>(packed);
+    for (size_t j = i; j < n_packed / 2; j += stride) p2[j] = make_ulonglong2(INF_KEY, INF_KEY);
+    if (i == 0 && (n_packed & 1)) packed[n_packed - 1] = INF_KEY;
+    for (size_t j = i; j < n_words; j += stride) bitmap[j] = 0u;
+    for (size_t j = i; j < n_dirty; j += stride) dirty[j] = 0u;
+}
+
+// K0: seed each source (Alg. 2: d(s) = 0, pq.push(s) by the owner of s).
+__global__ void k_seed(SolveLaunch L) {
+    const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s == 0 && L.hold_pending) atomicAdd(&L.hdr->pending, 1ull);
+    if (s >= L.S) return;
+    const uint32_t src = L.sources[s];
+    if (src >= L.V) {
+        set_status(L.hdr, SSSP_EINVAL);
+        return;
+    }
+    L.packed[(size_t)s * L.V + src] = SRC_KEY;
+    atomicOr(&L.bitmap[(size_t)s * L.words + (src >> 5)], 1u << (src & 31u));
+    const uint32_t p = src / L.B;
+    const uint32_t q = p * L.split + (src - p * L.B) / L.Bq;
+    atomicAdd(&L.hdr->pending, 1ull);
+    __threadfence();
+    L.dirty[(size_t)s * L.Q + q] = 1u;
+}
+
+template <class W>
+__global__ void k_unpack(const unsigned long long* __restrict__ packed, size_t n, uint32_t* __restrict__ dist,
+                         uint32_t* __restrict__ pred) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const unsigned long long k = packed[i];
+        dist[i] = k == INF_KEY ? W::inf_out() : (uint32_t)(k >> 32);
+        if (pred) pred[i] = k == INF_KEY ? NONE : (uint32_t)k;
+    }
+}
+
+// K4: persistent, static ownership: block b owns units b, b+grid, b+2*grid, ...
+template <class W>
+__global__ void __launch_bounds__(1024) k_solve(SolveLaunch L) {
+    extern __shared__ uint32_t dsm[];
+    __shared__ uint32_t wsum[32];
+    __shared__ Scalars sc;
+    const uint32_t Qw = (L.Q + 31u) / 32u;
+    const Smem sm = carve(dsm, L.tile, Qw, wsum, &sc);
+    for (uint32_t i = threadIdx.x; i < Qw; i += blockDim.x) sm.touched[i] = 0u;
+    __syncthreads();
+
+    const uint32_t U = L.S * L.Q;
+    const uint32_t nu = blockIdx.x < U ? (U - 1u - blockIdx.x) / gridDim.x + 1u : 0u;
+    uint32_t rr = 0, backoff = 32;
+    uint64_t idle_start = 0;
+    const uint64_t t_begin = globaltimer_ns();
+    Counters cnt = {};
+    Ctx c;
+    c.row_ptr = L.row_ptr;
+    c.col = L.col;
+    c.w = L.w;
+    c.V = L.V;
+    c.hdr = L.hdr;
+    c.delta = L.delta_bits;
+    c.tile = L.tile;
+    c.B = L.B;
+    c.Bq = L.Bq;
+    c.split = L.split;
+    c.Qw = Qw;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            int pick = -1;
+            if (ld_relaxed(&L.hdr->abort_flag)) {
+                pick = -2;
+            } else if (globaltimer_ns() - t_begin > KERNEL_LIMIT_FACTOR * L.timeout_ns) {
+                // whole-kernel limit: even a busy block cannot run unbounded
+                set_status(L.hdr, SSSP_ETIMEOUT);
+                atomicExch(&L.hdr->abort_flag, 1u);
+                pick = -2;
+            } else {
+                for (uint32_t t = 0; t < nu; ++t) {
+                    uint32_t j = rr + t;
+                    if (j >= nu) j -= nu;
+                    const uint32_t uid = blockIdx.x + j * gridDim.x;
+                    if (ld_relaxed(&L.dirty[uid]) != 0u && atomicExch(&L.dirty[uid], 0u) != 0u) {
+                        pick = (int)uid;
+                        rr = (j + 1u == nu) ? 0u : j + 1u;
+                        break;
+                    }
+                }
+                if (pick >= 0) {
+                    __threadfence();  // doorbell before the inbox scan
+                    idle_start = 0;
+                    backoff = 32;
+                } else if (ld_relaxed(&L.hdr->pending) == 0ull) {
+                    pick = -2;  // nothing queued, nothing in flight: terminated
+                } else {
+                    const uint64_t now = globaltimer_ns();
+                    if (idle_start == 0) {
+                        idle_start = now;
+                    } else if (now - idle_start > L.timeout_ns) {
+                        set_status(L.hdr, SSSP_ETIMEOUT);
+                        atomicExch(&L.hdr->abort_flag, 1u);
+                        pick = -2;
+                    }
+                    if (pick == -1) {
+                        __nanosleep(backoff);
+                        if (backoff < 1024u) backoff *= 2u;
+                    }
+                }
+            }
+            sc.pick = pick;
+        }
+        __syncthreads();
+        const int pick = sc.pick;
+        __syncthreads();
+        if (pick == -2) break;
+        if (pick < 0) continue;
+        const uint32_t s = (uint32_t)pick / L.Q, q = (uint32_t)pick % L.Q;
+        const uint32_t p = q / L.split, k = q % L.split;
+        const uint32_t plo = p * L.B;
+        const uint32_t phi = min(plo + L.B, L.V);
+        const uint32_t lo = plo + k * L.Bq;
+        const uint32_t hi = min(lo + L.Bq, phi);
+        if (lo >= hi) continue;
+        c.packed = L.packed + (size_t)s * L.V;
+        c.bitmap = L.bitmap + (size_t)s * L.words;
+        c.dirty = L.dirty + (size_t)s * L.Q;
+        relax_round<W, true>(c, lo, hi, q, sm, cnt);
+    }
+    flush_counters(L.hdr, cnt);
+}
+
+// K5: persistent, dynamic: blocks pull whole problems from a work queue.
+template <class W>
+__global__ void __launch_bounds__(1024) k_batched(BatchLaunch L) {
+    extern __shared__ uint32_t dsm[];
+    __shared__ uint32_t wsum[32];
+    __shared__ Scalars sc;
+    const Smem sm = carve(dsm, L.tile, 0u, wsum, &sc);
+    Counters cnt = {};
+    Ctx c;
+    c.hdr = L.hdr;
+    c.delta = L.delta_bits;
+    c.tile = L.tile;
+    c.dirty = nullptr;
+    c.B = c.Bq = c.split = 1u;
+    c.Qw = 0;
+    const uint32_t T = blockDim.x, tid = threadIdx.x;
+    const uint64_t t_begin = globaltimer_ns();
+    for (;;) {
+        if (tid == 0) {
+            sc.prob = ld_relaxed(&L.hdr->abort_flag) ? ~0ull : atomicAdd(&L.hdr->work_next, 1ull);
+        }
+        __syncthreads();
+        const unsigned long long pi = sc.prob;
+        __syncthreads();
+        if (pi >= L.n_problems) break;
+        const BatchProblem P = L.probs[pi];
+        if (P.V == 0) continue;
+        c.row_ptr = L.row_ptr + P.row_off;
+        c.col = L.col + P.edge_off;
+        c.w = L.w + P.edge_off;
+        c.V = P.V;
+        c.packed = L.packed + P.out_off;
+        c.bitmap = L.bitmap + P.bm_off;
+        const uint32_t words = (P.V + 31u) / 32u;
+        for (uint32_t i = tid; i < P.V; i += T) c.packed[i] = INF_KEY;
+        for (uint32_t i = tid; i < words; i += T) c.bitmap[i] = 0u;
+        __syncthreads();
+        if (tid == 0) {
+            if (P.src < P.V) {
+                c.packed[P.src] = SRC_KEY;
+                c.bitmap[P.src >> 5] = 1u << (P.src & 31u);
+            } else {
+                set_status(L.hdr, SSSP_EINVAL);
+            }
+        }
+        __syncthreads();
+        for (;;) {
+            const uint32_t found = relax_round<W, false>(c, 0u, P.V, 0u, sm, cnt);
+            if (tid == 0) {
+                int go = found != 0u;
+                if (go && globaltimer_ns() - t_begin > KERNEL_LIMIT_FACTOR * L.timeout_ns) {
+                    set_status(L.hdr, SSSP_ETIMEOUT);
+                    atomicExch(&L.hdr->abort_flag, 1u);
+                    go = 0;
+                }
+                sc.pick = go;
+            }
+            __syncthreads();
+            const int go = sc.pick;
+            __syncthreads();
+            if (!go) break;
+        }
+        uint32_t* dist = L.dist + P.out_off;
+        uint32_t* pred = L.pred ? L.pred + P.out_off : nullptr;
+        for (uint32_t i = tid; i < P.V; i += T) {
+            const unsigned long long k = ld_relaxed(&c.packed[i]);
+            dist[i] = k == INF_KEY ? W::inf_out() : (uint32_t)(k >> 32);
+            if (pred) pred[i] = k == INF_KEY ? NONE : (uint32_t)k;
+        }
+        __syncthreads();
+    }
+    flush_counters(L.hdr, cnt);
+}
+
+template <class K>
+cudaError_t set_smem(K kernel, size_t smem) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+}  // namespace
+
+size_t relax_smem_bytes(uint32_t tile, uint32_t Q) {
+    return (size_t)(4u * tile + 1u) * 4u + (size_t)((Q + 31u) / 32u) * 4u;
+}
+
+cudaError_t relax_max_blocks_per_sm(int wtype, uint32_t threads, uint32_t tile, uint32_t Q, int* out) {
+    const size_t smem = relax_smem_bytes(tile, Q);
+    cudaError_t e;
+    if (wtype == SSSP_W_F32) {
+        if ((e = set_smem(k_solve<WF32>, smem)) != cudaSuccess) return e;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_solve<WF32>, (int)threads, smem);
+    }
+    if ((e = set_smem(k_solve<WU32>, smem)) != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_solve<WU32>, (int)threads, smem);
+}
+
+cudaError_t launch_solve(const SolveLaunch& L, cudaStream_t st) {
+    cudaError_t e;
+    const size_t n_packed = (size_t)L.S * L.V;
+    const size_t n_words = (size_t)L.S * L.words;
+    const size_t n_dirty = (size_t)L.S * L.Q;
+    if ((e = cudaMemsetAsync(L.hdr, 0, WS_HEADER_BYTES, st)) != cudaSuccess) return e;
+    {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const size_t want = (n_packed / 2 + 255) / 256;
+        const unsigned blocks = (unsigned)std::min<size_t>(std::max<size_t>(want, 1), (size_t)sms * 8);
+        k_init_fill<<<blocks, 256, 0, st>>>(L.packed, n_packed, L.bitmap, n_words, L.dirty, n_dirty);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        k_seed<<<(L.S + 127) / 128, 128, 0, st>>>(L);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    const size_t smem = relax_smem_bytes(L.tile, L.Q);
+    void* args[] = {const_cast<SolveLaunch*>(&L)};
+    if (L.ev_begin && (e = cudaEventRecord(L.ev_begin, st)) != cudaSuccess) return e;
+    if (L.wtype == SSSP_W_F32) {
+        if ((e = set_smem(k_solve<WF32>, smem)) != cudaSuccess) return e;
+        e = cudaLaunchCooperativeKernel((const void*)k_solve<WF32>, dim3(L.grid), dim3(L.threads), args, smem, st);
+    } else {
+        if ((e = set_smem(k_solve<WU32>, smem)) != cudaSuccess) return e;
+        e = cudaLaunchCooperativeKernel((const void*)k_solve<WU32>, dim3(L.grid), dim3(L.threads), args, smem, st);
+    }
+    if (e != cudaSuccess) return e;
+    if (L.ev_end && (e = cudaEventRecord(L.ev_end, st)) != cudaSuccess) return e;
+    {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const unsigned blocks = (unsigned)std::min<size_t>(std::max<size_t>((n_packed + 255) / 256, 1), (size_t)sms * 8);
+        if (L.wtype == SSSP_W_F32)
+            k_unpack<WF32><<<blocks, 256, 0, st>>>(L.packed, n_packed, L.dist, L.pred);
+        else
+            k_unpack<WU32><<<blocks, 256, 0, st>>>(L.packed, n_packed, L.dist, L.pred);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t batched_max_blocks_per_sm(int wtype, uint32_t threads, uint32_t tile, int* out) {
+    const size_t smem = relax_smem_bytes(tile, 0);
+    cudaError_t e;
+    if (wtype == SSSP_W_F32) {
+        if ((e = set_smem(k_batched<WF32>, smem)) != cudaSuccess) return e;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_batched<WF32>, (int)threads, smem);
+    }
+    if ((e = set_smem(k_batched<WU32>, smem)) != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_batched<WU32>, (int)threads, smem);
+}
+
+cudaError_t launch_batched(const BatchLaunch& L, cudaStream_t st) {
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(L.hdr, 0, WS_HEADER_BYTES, st)) != cudaSuccess) return e;
+    // the dynamic shared-memory limit was raised by batched_max_blocks_per_sm (not a stream
+    // operation, so it stays outside any graph capture)
+    const size_t smem = relax_smem_bytes(L.tile, 0);
+    if (L.ev_begin && (e = cudaEventRecord(L.ev_begin, st)) != cudaSuccess) return e;
+    if (L.wtype == SSSP_W_F32)
+        k_batched<WF32><<<L.grid, L.threads, smem, st>>>(L);
+    else
+        k_batched<WU32><<<L.grid, L.threads, smem, st>>>(L);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (L.ev_end && (e = cudaEventRecord(L.ev_end, st)) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+}  // namespace sssp

@@ -1,0 +1,91 @@
+"""The C ABI library loads without a GPU, exports every entry point that
+include/*.h declares, and rejects bad arguments on the host (no GPU work)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+import paper_2103_12012_gb300 as sssp
+from paper_2103_12012_gb300 import _build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    _build.build()
+    return sssp.lib()
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(sssp_[a-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    return names
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared_functions()
+    assert {"sssp_prune", "sssp_solve", "sssp_solve_batched", "sssp_backward"} <= names
+    for n in sorted(names):
+        assert hasattr(L, n), n
+    assert set(sssp._SIGS) == names, "binding and header disagree"
+
+
+def test_status_strings(L):
+    assert sssp.status_string(sssp.SSSP_OK) == "ok"
+    assert sssp.status_string(sssp.SSSP_ETIMEOUT) == "device wait timed out"
+    assert L.sssp_version().decode().startswith("libsssp")
+
+
+def _graph(V=10, E=0, P=1, wtype=0):
+    return sssp.SsspGraph(V, E, 16, 16 if E else None, 16 if E else None, wtype, P)
+
+
+def test_host_argument_checks_without_gpu(L):
+    g = _graph()
+    opt = sssp.options()
+    # NULL graph, zero sources, bad partition counts, bad weight type: rejected before any launch
+    assert L.sssp_solve(None, 16, 1, 16, None, None, 16, 1 << 20, None) == sssp.SSSP_EINVAL
+    assert L.sssp_solve(ctypes.byref(g), 16, 0, 16, None, None, 16, 1 << 20, None) == sssp.SSSP_EINVAL
+    for bad in (_graph(P=0), _graph(P=11), _graph(wtype=7), _graph(V=0)):
+        assert L.sssp_solve(ctypes.byref(bad), 16, 1, 16, None, None, 16, 1 << 20, None) == sssp.SSSP_EINVAL
+        assert L.sssp_solve_workspace_size(ctypes.byref(bad), 1, None) == 0
+    # bad options
+    for o in (sssp.options(threads=100), sssp.options(threads=2048), sssp.options(tile=8), sssp.options(delta=-1)):
+        assert L.sssp_solve_workspace_size(ctypes.byref(g), 1, ctypes.byref(o)) == 0
+    # too-small workspace
+    need = L.sssp_solve_workspace_size(ctypes.byref(g), 2, ctypes.byref(opt))
+    assert need > 0
+    assert L.sssp_solve(ctypes.byref(g), 16, 2, 16, None, ctypes.byref(opt), 256, need - 1, None) == sssp.SSSP_ENOMEM
+    assert L.sssp_prune(ctypes.byref(g), 3, 16, None, None) == sssp.SSSP_EINVAL
+    assert L.sssp_build_csr(0, 0, None, None, None, 0, None, None, None, None, None, None, 0, None) == sssp.SSSP_EINVAL
+    assert L.sssp_backward(ctypes.byref(g), 0, 16, 16, 16, 16, 1 << 20, None) == sssp.SSSP_EINVAL
+
+
+def test_workspace_sizes_scale(L):
+    g = sssp.SsspGraph(4194304, 67108864, 16, 16, 16, 0, 148)
+    one = L.sssp_solve_workspace_size(ctypes.byref(g), 1, None)
+    eight = L.sssp_solve_workspace_size(ctypes.byref(g), 8, None)
+    # packed words dominate: 8 bytes per vertex per source
+    assert 8 * 4194304 <= one < 8 * 4194304 * 1.1
+    assert abs(eight - 8 * one) < 8 * 4096
+    assert L.sssp_build_csr_workspace_size(1000, 5000) > 5000 * 36
+    assert L.sssp_backward_workspace_size(1000, 5000, 3) >= 3 * 1000 * 13 + 5000 * 8
+
+
+def test_batch_tables_checked_on_host(L):
+    graphs = (sssp.SsspBatchGraph * 1)(sssp.SsspBatchGraph(0, 0, 10, 0))
+    import numpy as np
+    pg = np.array([0, 0], np.uint32)
+    ps = np.array([3, 11], np.uint32)  # 11 >= V: invalid
+    b = sssp.SsspBatch(1, 2, ctypes.cast(graphs, ctypes.c_void_p), pg.ctypes.data, ps.ctypes.data, 16, 16, 16, 0,
+                       16, None)
+    assert L.sssp_batch_workspace_size(ctypes.byref(b), None) == 0
+    ps[1] = 9
+    assert L.sssp_batch_workspace_size(ctypes.byref(b), None) > 0

@@ -1,0 +1,313 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle on seeded inputs.
+
+Sizes span several tiles and partition blocks with ragged tails.  Integer
+results (CSR, keep masks, witnesses, uint32 distances, predecessors) must be
+bit-exact; float32 distances must be bit-exact as well (both sides round every
+d(u)+w once to float32 and reach the same fixpoint), which is tighter than
+the 1e-6 relative bound the float32 workload allows.  Gradients: float64
+accumulation on both sides, compared at rtol 1e-5 (float32 output rounding).
+"""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def sssp():
+    import paper_2103_12012_gb300 as m
+    m.lib()
+    return m
+
+
+def u32(t):
+    return t.detach().cpu().numpy().view(np.uint32)
+
+
+def raw_graph(seed, V, E, f32=False, wlo=1, whi=255, loops=True):
+    rng = np.random.default_rng(seed)
+    src = rng.integers(0, V, E).astype(np.uint32)
+    dst = rng.integers(0, V, E).astype(np.uint32)
+    if not loops:
+        dst = np.where(src == dst, (dst + 1) % V, dst).astype(np.uint32)
+    w = rng.uniform(0.5, 2.0, E).astype(np.float32) if f32 else rng.integers(wlo, whi + 1, E).astype(np.uint32)
+    return src, dst, w
+
+
+def check_solve(sssp, g_dev, ref, sources, opts=None):
+    dist, pred, st, stats = sssp.solve(g_dev, np.asarray(sources, np.uint32), opts)
+    assert st == sssp.SSSP_OK
+    for i, s in enumerate(sources):
+        d, p, _ = oracle.dijkstra(ref, int(s))
+        assert np.array_equal(u32(dist[i]), d.view(np.uint32)), f"dist mismatch, source {s}"
+        assert np.array_equal(u32(pred[i]), p), f"pred mismatch, source {s}"
+    return stats
+
+
+# --------------------------------------------------------------------- K1 / K2
+
+@pytest.mark.parametrize("seed,V,E,f32", [(0, 1000, 20000, False), (1, 5000, 3000, False), (2, 777, 50000, True),
+                                          (3, 1, 5, False), (4, 64, 0, False), (5, 100000, 400000, False)])
+def test_csr_build_parity(sssp, seed, V, E, f32):
+    src, dst, w = raw_graph(seed, V, E, f32=f32, whi=9)
+    ref = oracle.csr(V, src, dst, w)
+    g = sssp.build_csr(V, src, dst, w)
+    assert g.E == ref.E
+    assert np.array_equal(u32(g.row_ptr), ref.row_ptr)
+    if ref.E:
+        assert np.array_equal(u32(g.col), ref.col)
+        assert np.array_equal(u32(g.w), ref.w.view(np.uint32))
+        assert np.array_equal(u32(g.eid), ref.eid)
+
+
+def test_csr_build_rejects_bad_ids_and_weights(sssp):
+    with pytest.raises(sssp.SsspError):
+        sssp.build_csr(10, np.array([0, 10], np.uint32), np.array([1, 2], np.uint32), np.array([1, 1], np.uint32))
+    with pytest.raises(sssp.SsspError):
+        sssp.build_csr(10, np.array([0, 1], np.uint32), np.array([1, 2], np.uint32), np.array([1, 0], np.uint32))
+
+
+@pytest.mark.parametrize("V,P", [(16384, 4), (1000, 7), (4194, 148), (10, 10)])
+def test_partition_parity(sssp, V, P):
+    src, dst, w = raw_graph(11, V, 8 * V)
+    ref = oracle.csr(V, src, dst, w)
+    g = sssp.build_csr(V, src, dst, w, partitions=P)
+    b, inter = sssp.partition(g)
+    rb, ri = oracle.partition(V, P, ref)
+    assert np.array_equal(u32(b), rb)
+    assert np.array_equal(inter.cpu().numpy().astype(np.uint64), ri)
+
+
+# ------------------------------------------------------------------------ K3
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_prune_parity_er16k(sssp, mode):
+    g0, _, P = gg.workload_er16k()
+    ref = oracle.csr_of(g0)
+    g = sssp.build_csr(g0.V, g0.src, g0.dst, g0.w, partitions=P)
+    keep, wit = sssp.prune(g, mode)
+    rk, rw = oracle.trishla(ref, P, mode)
+    assert np.array_equal(keep.cpu().numpy(), rk)
+    assert np.array_equal(u32(wit), rw)
+
+
+@pytest.mark.parametrize("seed,V,E,P,mode,f32", [(20, 300, 6000, 3, 0, False), (21, 300, 6000, 3, 1, False),
+                                                 (22, 2000, 30000, 5, 1, True), (23, 50, 2000, 1, 0, True)])
+def test_prune_parity_dense_and_f32(sssp, seed, V, E, P, mode, f32):
+    src, dst, w = raw_graph(seed, V, E, f32=f32, whi=30)
+    ref = oracle.csr(V, src, dst, w)
+    g = sssp.build_csr(V, src, dst, w, partitions=P)
+    keep, wit = sssp.prune(g, mode)
+    rk, rw = oracle.trishla(ref, P, mode)
+    assert (rk == 0).any()
+    assert np.array_equal(keep.cpu().numpy(), rk)
+    assert np.array_equal(u32(wit), rw)
+
+
+def test_compact_and_solve_on_pruned_graph(sssp):
+    g0, srcs, P = gg.workload_er16k()
+    ref = oracle.csr_of(g0)
+    g = sssp.build_csr(g0.V, g0.src, g0.dst, g0.w, partitions=P)
+    keep, _ = sssp.prune(g, 0)
+    gp = sssp.compact(g, keep)
+    rk, _ = oracle.trishla(ref, P, 0)
+    rp = oracle.compact(ref, rk)
+    assert gp.E == rp.E
+    assert np.array_equal(u32(gp.row_ptr), rp.row_ptr)
+    assert np.array_equal(u32(gp.col), rp.col)
+    assert np.array_equal(u32(gp.w), rp.w)
+    # pruned edges are never tight, so distances and canonical predecessors are unchanged (Sec. III.B)
+    check_solve(sssp, gp, ref, [0, 1, 9999])
+
+
+# ------------------------------------------------------------------- K0/K4
+
+def test_solve_er16k_p4(sssp):
+    g0, srcs, P = gg.workload_er16k()
+    ref = oracle.csr_of(g0)
+    g = sssp.build_csr(g0.V, g0.src, g0.dst, g0.w, partitions=P)
+    stats = check_solve(sssp, g, ref, srcs.tolist())
+    assert stats["edges_scanned"] >= ref.E * 0.5  # most of the graph is reachable and scanned
+
+
+@pytest.mark.parametrize("P", [1, 2, 4, 7, 148])
+@pytest.mark.parametrize("split", [1, 3])
+def test_solve_partition_counts(sssp, P, split):
+    V = 5000
+    src, dst, w = raw_graph(30 + P, V, 40000)
+    ref = oracle.csr(V, src, dst, w)
+    g = sssp.build_csr(V, src, dst, w, partitions=P)
+    check_solve(sssp, g, ref, [0, 4999, 2500, 0], sssp.options(split=split))
+
+
+@pytest.mark.parametrize("opts", [dict(threads=128, tile=32, delta=1), dict(threads=256, tile=64, delta=10),
+                                  dict(threads=1024, tile=4096, delta=1e9), dict(threads=512, tile=100, delta=50,
+                                                                                 blocks_per_sm=1)])
+def test_solve_schedule_does_not_change_result(sssp, opts):
+    V = 20000
+    src, dst, w = raw_graph(40, V, 160000)
+    ref = oracle.csr(V, src, dst, w)
+    g = sssp.build_csr(V, src, dst, w, partitions=16)
+    check_solve(sssp, g, ref, [3, 19999, 12345], sssp.options(**opts))
+
+
+def test_solve_f32_bit_exact(sssp):
+    g0 = gg.rmat(gg.BASE_SEED + 50, 14, 8 << 14, wf32=(0.5, 2.0, 1e-4))
+    ref = oracle.csr_of(g0)
+    g = sssp.upload_csr(ref.V, ref.row_ptr, ref.col, ref.w, partitions=12)
+    srcs = gg.pick_sources(gg.BASE_SEED + 50, g0, 5)
+    check_solve(sssp, g, ref, srcs.tolist(), sssp.options(delta=0.25))
+
+
+def test_solve_grid_closed_form_and_unreachable(sssp):
+    # constant-weight grid: d = c*(r+q) from corner 0; plus a second component never reached
+    R, C, c = 60, 70, 7
+    g0 = gg.grid(1, R, C, c, c)
+    src = np.concatenate([g0.src, np.array([R * C, R * C + 1], np.uint32)])
+    dst = np.concatenate([g0.dst, np.array([R * C + 1, R * C + 2], np.uint32)])
+    w = np.concatenate([g0.w, np.array([1, 1], np.uint32)])
+    V = R * C + 3
+    ref = oracle.csr(V, src, dst, w)
+    g = sssp.build_csr(V, src, dst, w, partitions=9)
+    dist, pred, st, _ = sssp.solve(g, np.array([0], np.uint32))
+    d = u32(dist[0])
+    r, q = np.divmod(np.arange(R * C), C)
+    assert np.array_equal(d[:R * C], (c * (r + q)).astype(np.uint32))
+    assert (d[R * C:] == 0xFFFFFFFF).all() and (u32(pred[0])[R * C:] == 0xFFFFFFFF).all()
+    check_solve(sssp, g, ref, [0, R * C])
+
+
+def test_solve_tiny_and_isolated(sssp):
+    g = sssp.build_csr(1, np.zeros(0, np.uint32), np.zeros(0, np.uint32), np.zeros(0, np.uint32))
+    dist, pred, st, _ = sssp.solve(g, np.array([0], np.uint32))
+    assert u32(dist).tolist() == [[0]] and u32(pred).tolist() == [[0xFFFFFFFF]]
+    src = np.array([0, 1], np.uint32)
+    dst = np.array([1, 2], np.uint32)
+    ref = oracle.csr(40, src, dst, np.array([5, 6], np.uint32))
+    g = sssp.build_csr(40, src, dst, np.array([5, 6], np.uint32), partitions=40)
+    check_solve(sssp, g, ref, [0, 39, 2])
+
+
+def test_solve_overflow_status(sssp):
+    w = np.array([0xFFFFFFFE, 2, 1], np.uint32)
+    src, dst = np.array([0, 1, 0], np.uint32), np.array([1, 2, 3], np.uint32)
+    ref = oracle.csr(4, src, dst, w)
+    g = sssp.build_csr(4, src, dst, w)
+    dist, pred, st, _ = sssp.solve(g, np.array([0], np.uint32), check=False)
+    assert st == sssp.SSSP_EOVERFLOW
+    d, p, rst = oracle.dijkstra(ref, 0)
+    assert rst == oracle.OVERFLOW
+    assert np.array_equal(u32(dist[0]), d) and np.array_equal(u32(pred[0]), p)
+
+
+def test_solve_bad_source_is_reported(sssp):
+    src, dst, w = raw_graph(5, 100, 500)
+    g = sssp.build_csr(100, src, dst, w)
+    dist, pred, st, _ = sssp.solve(g, np.array([3, 100], np.uint32), check=False)
+    assert st == sssp.SSSP_EINVAL
+    assert (u32(dist[1]) == 0xFFFFFFFF).all()
+
+
+def test_solve_wait_limit_returns_timeout_and_device_stays_usable(sssp):
+    """The termination count is held one above its true value (a count that nothing will
+    release), so every block's idle wait must run out: status SSSP_ETIMEOUT, kernel returns."""
+    V = 3000
+    src, dst, w = raw_graph(6, V, 20000)
+    ref = oracle.csr(V, src, dst, w)
+    g = sssp.build_csr(V, src, dst, w, partitions=4)
+    o = sssp.options(timeout_ns=50_000_000, flags=sssp.FLAG_TEST_HOLD_PENDING)
+    _, _, st, _ = sssp.solve(g, np.array([0], np.uint32), o, check=False)
+    assert st == sssp.SSSP_ETIMEOUT
+    check_solve(sssp, g, ref, [0])
+
+
+# ------------------------------------------------------------------------ K5
+
+def test_batched_parity_and_graph_replay(sssp):
+    graphs, sources = [], []
+    for k in range(24):
+        t, n = gg.batch_params(gg.BASE_SEED + 77, k, 6.0, 12.0)
+        ms = gg.member_seed(gg.BASE_SEED + 77, k)
+        if t == 0:
+            g0 = gg.erdos_renyi(ms, n, 8 * n, 1, 255)
+        else:
+            import math
+            g0 = gg.rmat(ms, max(1, math.ceil(math.log2(n))), 8 * n, n=n)
+        graphs.append(oracle.csr_of(g0))
+        sources.append(gg.pick_sources(ms, g0, 4))
+    b = sssp.Batch(graphs, sources, sssp.options(tile=256))
+    b.solve()
+    st, stats = b.status()
+    assert st == sssp.SSSP_OK
+
+    def check():
+        for i in range(b.n_problems):
+            gi, s = int(b.prob_graph[i]), int(b.prob_source[i])
+            d, p, _ = oracle.dijkstra(graphs[gi], s)
+            bd, bp = b.result(i)
+            assert np.array_equal(u32(bd), d) and np.array_equal(u32(bp), p), (i, gi, s)
+
+    check()
+    b.dist.fill_(0)
+    b.pred.fill_(0)
+    b.make_plan()
+    for _ in range(2):
+        b.replay()
+    st, _ = b.status()
+    assert st == sssp.SSSP_OK
+    check()
+
+
+def test_batched_equals_single_solves(sssp):
+    g0, srcs, _ = gg.workload_er16k()
+    ref = oracle.csr_of(g0)
+    srcs = np.array([0, 5, 77, 16383], np.uint32)
+    b = sssp.Batch([ref], [srcs])
+    b.solve()
+    g = sssp.upload_csr(ref.V, ref.row_ptr, ref.col, ref.w, partitions=4)
+    dist, pred, _, _ = sssp.solve(g, srcs)
+    for i in range(4):
+        bd, bp = b.result(i)
+        assert torch.equal(bd, dist[i]) and torch.equal(bp, pred[i])
+
+
+# ------------------------------------------------------------------------ K6
+
+@pytest.mark.parametrize("scale,S", [(10, 3), (14, 8)])
+def test_backward_parity(sssp, scale, S):
+    g0 = gg.rmat(gg.BASE_SEED + 60 + scale, scale, 8 << scale, wf32=(0.5, 2.0, 1e-4))
+    ref = oracle.csr_of(g0)
+    g = sssp.upload_csr(ref.V, ref.row_ptr, ref.col, ref.w, partitions=8)
+    srcs = gg.pick_sources(gg.BASE_SEED + 60, g0, S)
+    dist, pred, st, _ = sssp.solve(g, srcs)
+    gup = torch.from_numpy(gg.normal_f32(scale, (S, ref.V))).cuda()
+    grad = sssp.backward(g, pred, gup).cpu().numpy().astype(np.float64)
+    rd = np.stack([oracle.dijkstra(ref, int(s))[0] for s in srcs])
+    rp = np.stack([oracle.dijkstra(ref, int(s))[1] for s in srcs])
+    assert np.array_equal(u32(pred), rp)
+    rg = oracle.tree_grad(ref, rd, rp, gup.cpu().numpy())
+    assert np.allclose(grad, rg, rtol=1e-5, atol=1e-6 * np.abs(rg).max())
+    assert (grad[rg == 0] == 0).all()
+
+
+def test_autograd_function(sssp):
+    g0 = gg.rmat(gg.BASE_SEED + 61, 9, 8 << 9, wf32=(0.5, 2.0, 1e-4))
+    ref = oracle.csr_of(g0)
+    g = sssp.upload_csr(ref.V, ref.row_ptr, ref.col, ref.w, partitions=2)
+    srcs_np = gg.pick_sources(gg.BASE_SEED + 61, g0, 2)
+    srcs = torch.from_numpy(srcs_np.view(np.int32)).cuda()
+    w = g.w.clone().requires_grad_(True)
+    F = sssp.sssp_function()
+    dist = F.apply(w, g, srcs)
+    gup = torch.from_numpy(gg.normal_f32(3, tuple(dist.shape))).cuda()
+    finite = torch.isfinite(dist)
+    (torch.where(finite, dist, torch.zeros_like(dist)) * gup).sum().backward()
+    rd = np.stack([oracle.dijkstra(ref, int(s))[0] for s in srcs_np])
+    rp = np.stack([oracle.dijkstra(ref, int(s))[1] for s in srcs_np])
+    rg = oracle.tree_grad(ref, rd, rp, gup.cpu().numpy())
+    assert np.allclose(w.grad.cpu().numpy(), rg, rtol=1e-5, atol=1e-6 * np.abs(rg).max())
