@@ -204,6 +204,33 @@ sssp_status sssp_solve(const sssp_graph* g, const uint32_t* sources, uint32_t S,
  */
 sssp_status sssp_workspace_status(const void* ws, sssp_stream_t stream, sssp_stats* stats);
 
+/* ------------------------------------------------------ no-allocation solve */
+
+/* Bytes of the fixed device array that backs sssp_solve_noalloc (reserved on
+ * every GPU that loads the library, until the process exits). */
+#define SSSP_NOALLOC_SCRATCH_BYTES (8u << 20)
+
+/*
+ * sssp_solve for callers that cannot allocate device memory.  The paper has
+ * no counterpart: this is a convenience of the library.  Some callers, such as
+ * a plugin or user-defined function inside a host application that owns every
+ * device allocation and hands extensions only their input and output buffers,
+ * have no way to provide sssp_solve's workspace.  This call takes its scratch
+ * from a fixed array of SSSP_NOALLOC_SCRATCH_BYTES that the library reserves
+ * on each device, so it allocates nothing.
+ *   g, sources, S, dist, pred, opt : as for sssp_solve
+ *   status_out : device [1] uint32 (may be NULL), receives the solve's device-side
+ *                sssp_status, copied on `stream` after the solve
+ * Returns SSSP_ENOMEM (nothing launched) if sssp_solve_workspace_size(g, S, opt)
+ * exceeds SSSP_NOALLOC_SCRATCH_BYTES.  The first call on a device resolves the
+ * array's address (cudaGetSymbolAddress, with that device current); make it
+ * before any stream capture.  All calls share the array, which keeps the last
+ * call's contents (each call re-initialises what it reads): calls that overlap
+ * on the GPU race and must be ordered by the caller.
+ */
+sssp_status sssp_solve_noalloc(const sssp_graph* g, const uint32_t* sources, uint32_t S, void* dist, uint32_t* pred,
+                               const sssp_options* opt, uint32_t* status_out, sssp_stream_t stream);
+
 /* ------------------------------------------------------------ K5 batched */
 
 /* One graph of a batch: its CSR lives inside shared concatenated arrays. */

@@ -70,6 +70,7 @@ _SIGS = {
     "sssp_solve_workspace_size": (sz, [P, u32, P]),
     "sssp_solve": (i32, [P, P, u32, P, P, P, P, sz, P]),
     "sssp_workspace_status": (i32, [P, P, P]),
+    "sssp_solve_noalloc": (i32, [P, P, u32, P, P, P, P, P]),
     "sssp_batch_workspace_size": (sz, [P, P]),
     "sssp_solve_batched": (i32, [P, P, P, sz, P]),
     "sssp_batch_plan_create": (i32, [P, P, P, sz, P, P]),
