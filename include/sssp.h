@@ -86,8 +86,9 @@ typedef struct {
     uint32_t tile;         /* most vertices one block takes from its inbox per round: 32..4096 (default 1024) */
     uint32_t split;        /* blocks sharing one partition, each owning a sub-block of its vertices (default 1) */
     double delta;          /* bucket width: a round takes inbox vertices with dist < min dist + delta
-                              (default: uint32 -> 4 x mean edge weight estimate 128, float32 -> 1.0) */
-    uint64_t timeout_ns;   /* limit on a block's continuous idle wait (default 20 s) */
+                              (default: uint32 -> 8, float32 -> 0.0625) */
+    uint64_t timeout_ns;   /* limit on a block's continuous idle wait (default 20 s); a persistent
+                              kernel also stops after 3 x timeout_ns in total */
     uint32_t flags;        /* SSSP_FLAG_* */
     uint32_t reserved;
     void* ev_relax_begin;  /* cudaEvent_t or NULL: recorded on `stream` right before the relaxation kernel */
@@ -108,7 +109,7 @@ typedef struct {
     uint64_t rounds;           /* rounds run by all blocks */
     uint64_t vertices;         /* vertices processed (taken from an inbox) */
     uint64_t remote_activations; /* activations of a vertex owned by another unit (messages, Alg. 3 send_msg) */
-    uint64_t reserved;
+    uint64_t idle_us;          /* microseconds blocks spent waiting with no unit to process, summed over blocks */
 } sssp_stats;
 
 const char* sssp_status_string(sssp_status s);

@@ -42,10 +42,10 @@ class SsspOptions(ctypes.Structure):
 
 class SsspStats(ctypes.Structure):
     _fields_ = [("edges_scanned", u64), ("atomics", u64), ("improved", u64), ("activations", u64),
-                ("rounds", u64), ("vertices", u64), ("remote_activations", u64), ("reserved", u64)]
+                ("rounds", u64), ("vertices", u64), ("remote_activations", u64), ("idle_us", u64)]
 
     def as_dict(self):
-        return {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "reserved"}
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
 class SsspBatchGraph(ctypes.Structure):

@@ -135,7 +135,7 @@ __global__ void k_partition(uint32_t V, uint32_t P, unsigned long long B, const 
     const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t p = gtid; p <= P; p += stride)
-        bounds[p] = (uint32_t)std::min<unsigned long long>((unsigned long long)p * B, V);
+        bounds[p] = (uint32_t)((unsigned long long)p * B < V ? (unsigned long long)p * B : V);
     if (!inter) return;
     for (uint32_t u = gtid; u < V; u += stride) {
         const uint32_t pu = (uint32_t)(u / B);

@@ -44,6 +44,8 @@ namespace {
 
 constexpr unsigned long long SRC_KEY = 0x00000000FFFFFFFFull;  // dist 0, pred NONE
 constexpr uint64_t KERNEL_LIMIT_FACTOR = 3;  // whole-kernel wall-clock limit = 3 x idle limit
+constexpr int EDGE_BATCH = 4;                // edges in flight per thread in phase E
+constexpr unsigned long long ROUND_RESERVE = 1ull << 32;  // termination counts reserved per round (> edges)
 
 __device__ __forceinline__ uint32_t atom_or_release(uint32_t* p, uint32_t v) {
     uint32_t old;
@@ -132,7 +134,8 @@ struct Scalars {
 };
 
 struct Counters {
-    unsigned long long edges, atomics, improved, acts, rounds, verts, remote;
+    unsigned long long edges, acts, rounds, verts, idle_ns;  // kept by thread 0
+    uint32_t atomics, improved, remote;             // kept per thread (statistics only)
 };
 
 // Per-round view of one problem (one source on one graph).
@@ -175,6 +178,13 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
         sc.nclaim = 0;
         sc.act = 0;
         sc.bad = 0;
+        if (STATIC) {
+            // Reserve termination counts before this round can make any inbox bit
+            // visible (a round activates at most one vertex per relaxed edge, fewer
+            // than ROUND_RESERVE); the fence overlaps with the other threads' scan.
+            atomicAdd(&c.hdr->pending, ROUND_RESERVE);
+            __threadfence();
+        }
     }
     __syncthreads();
 
@@ -187,7 +197,7 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
             const uint32_t b = __ffs(bits) - 1u;
             bits &= bits - 1u;
             const uint32_t v = wd * 32u + b;
-            const uint32_t d = (uint32_t)(ld_relaxed(&c.packed[v]) >> 32);
+            const uint32_t d = (uint32_t)(__ldcg(&c.packed[v]) >> 32);
             lmin = min(lmin, d);
             ++lcnt;
             const uint32_t idx = atomicAdd(&sc.nlist, 1u);
@@ -205,145 +215,173 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
     }
     __syncthreads();
     const uint32_t found = sc.cnt;
-    if (found == 0) return 0;
-    const uint32_t thr = bucket_bound<W>(sc.dmin, c.delta);
+    uint32_t nsel = 0, te = 0;
+    if (found != 0) {
+        const uint32_t thr = bucket_bound<W>(sc.dmin, c.delta);
 
-    // ---- B: the near bucket, at most `tile` vertices
-    if (found <= c.tile) {
-        for (uint32_t i = tid; i < found; i += T)
-            if (sm.list_d[i] < thr) sm.sel_v[atomicAdd(&sc.nsel, 1u)] = sm.list_v[i];
-    } else {
-        for (uint32_t wd = wlo + tid; wd <= whi; wd += T) {
-            uint32_t bits = ld_relaxed(&c.bitmap[wd]) & range_mask(wd, lo, hi);
-            while (bits) {
-                const uint32_t b = __ffs(bits) - 1u;
-                bits &= bits - 1u;
-                const uint32_t v = wd * 32u + b;
-                if ((uint32_t)(ld_relaxed(&c.packed[v]) >> 32) < thr) {
-                    const uint32_t j = atomicAdd(&sc.nsel, 1u);
-                    if (j < c.tile) sm.sel_v[j] = v;
-                }
-            }
-        }
-    }
-    __syncthreads();
-    const uint32_t nsel = min(sc.nsel, c.tile);
-
-    // ---- C: take them off the inbox
-    uint32_t myclaim = 0;
-    for (uint32_t i = tid; i < nsel; i += T) {
-        const uint32_t v = sm.sel_v[i], bit = 1u << (v & 31u);
-        const uint32_t old = atom_and_acquire(&c.bitmap[v >> 5], ~bit);
-        if (old & bit)
-            ++myclaim;
-        else
-            sm.sel_v[i] = NONE;
-    }
-    // ---- D: distances and row extents of the taken vertices (same thread as its take)
-    for (uint32_t i = tid; i < nsel; i += T) {
-        const uint32_t u = sm.sel_v[i];
-        uint32_t deg = 0, beg = 0, du = 0;
-        if (u != NONE) {
-            du = (uint32_t)(ld_relaxed(&c.packed[u]) >> 32);
-            beg = __ldg(&c.row_ptr[u]);
-            deg = __ldg(&c.row_ptr[u + 1]) - beg;
-        }
-        sm.list_d[i] = du;
-        sm.list_v[i] = beg;
-        sm.sel_pref[i] = deg;
-    }
-    myclaim = warp_sum(myclaim);
-    if (lane == 0 && myclaim) atomicAdd(&sc.nclaim, myclaim);
-    __syncthreads();
-    const uint32_t te = block_scan_excl(sm.sel_pref, nsel, sm.wsum);
-    if (tid == 0) sm.sel_pref[nsel] = te;
-    if (STATIC) {
-        // reserve one termination count per edge before any new bit can be seen
-        if (tid == 0 && te) {
-            atomicAdd(&c.hdr->pending, (unsigned long long)te);
-            __threadfence();
-        }
-    }
-    __syncthreads();
-
-    // ---- E: relax all out-edges, edge-parallel
-    uint32_t lact = 0, bad = 0;
-    for (uint32_t k = tid; k < te; k += T) {
-        uint32_t a = 0, b = nsel;  // sel_pref[a] <= k < sel_pref[b]
-        while (b - a > 1u) {
-            const uint32_t m = (a + b) >> 1;
-            if (sm.sel_pref[m] <= k)
-                a = m;
-            else
-                b = m;
-        }
-        const uint32_t e = sm.list_v[a] + (k - sm.sel_pref[a]);
-        const uint32_t u = sm.sel_v[a], du = sm.list_d[a];
-        const uint32_t v = __ldg(&c.col[e]);
-        const uint32_t wt = __ldg(&c.w[e]);
-        if (!W::weight_ok(wt) || v >= c.V) {
-            bad |= 1u;
-            continue;
-        }
-        uint32_t cand;
-        if (!W::add(du, wt, cand)) {
-            bad |= 2u;
-            continue;
-        }
-        const unsigned long long key = ((unsigned long long)cand << 32) | u;
-        if (key < ld_relaxed(&c.packed[v])) {
-            ++cnt.atomics;
-            const unsigned long long old = atomicMin(&c.packed[v], key);
-            if (key < old && (uint32_t)(old >> 32) > cand) {
-                ++cnt.improved;
-                const uint32_t bit = 1u << (v & 31u);
-                const uint32_t ob = atom_or_release(&c.bitmap[v >> 5], bit);
-                if (!(ob & bit)) {
-                    ++lact;
-                    if (STATIC) {
-                        const uint32_t p = v / c.B;
-                        const uint32_t q = p * c.split + (v - p * c.B) / c.Bq;
-                        if (q != my_q) ++cnt.remote;
-                        atomicOr(&sm.touched[q >> 5], 1u << (q & 31u));
+        // ---- B: the near bucket, at most `tile` vertices
+        if (found <= c.tile) {
+            for (uint32_t i = tid; i < found; i += T)
+                if (sm.list_d[i] < thr) sm.sel_v[atomicAdd(&sc.nsel, 1u)] = sm.list_v[i];
+        } else {
+            for (uint32_t wd = wlo + tid; wd <= whi; wd += T) {
+                uint32_t bits = ld_relaxed(&c.bitmap[wd]) & range_mask(wd, lo, hi);
+                while (bits) {
+                    const uint32_t b = __ffs(bits) - 1u;
+                    bits &= bits - 1u;
+                    const uint32_t v = wd * 32u + b;
+                    if ((uint32_t)(__ldcg(&c.packed[v]) >> 32) < thr) {
+                        const uint32_t j = atomicAdd(&sc.nsel, 1u);
+                        if (j < c.tile) sm.sel_v[j] = v;
                     }
                 }
             }
         }
-    }
-    lact = warp_sum(lact);
-    bad = __reduce_or_sync(0xFFFFFFFFu, bad);
-    if (lane == 0) {
-        if (lact) atomicAdd(&sc.act, lact);
-        if (bad) atomicOr(&sc.bad, bad);
-    }
-    __syncthreads();
-    if (tid == 0) {
-        cnt.edges += te;
-        cnt.rounds += 1;
-        cnt.verts += sc.nclaim;
-        cnt.acts += sc.act;
-        if (sc.bad & 1u) set_status(c.hdr, SSSP_EINVAL);
-        if (sc.bad & 2u) set_status(c.hdr, SSSP_EOVERFLOW);
-    }
+        __syncthreads();
+        nsel = min(sc.nsel, c.tile);
 
-    // ---- F: settle the count, ring doorbells
-    if (STATIC) {
-        if (tid == 0) {
-            const long long d = (long long)sc.act - (long long)te - (long long)sc.nclaim;
-            if (d) atomicAdd(&c.hdr->pending, (unsigned long long)d);
+        // ---- C: take them off the inbox (acquire: the producers' packed-word
+        // updates are visible to the reads below); D: distances and row extents
+        uint32_t myclaim = 0;
+        for (uint32_t i = tid; i < nsel; i += T) {
+            uint32_t u = sm.sel_v[i];
+            const uint32_t bit = 1u << (u & 31u);
+            const uint32_t old = atom_and_acquire(&c.bitmap[u >> 5], ~bit);
+            uint32_t deg = 0, beg = 0, du = 0;
+            if (old & bit) {
+                ++myclaim;
+                du = (uint32_t)(__ldcg(&c.packed[u]) >> 32);
+                beg = __ldg(&c.row_ptr[u]);
+                deg = __ldg(&c.row_ptr[u + 1]) - beg;
+            } else {
+                sm.sel_v[i] = NONE;
+            }
+            sm.list_d[i] = du;
+            sm.list_v[i] = beg;
+            sm.sel_pref[i] = deg;
         }
-        __threadfence();  // new bits (set before the barrier above) before the doorbells
-        for (uint32_t wq = tid; wq < c.Qw; wq += T) {
-            uint32_t bits = sm.touched[wq];
-            if (!bits) continue;
-            sm.touched[wq] = 0;
-            while (bits) {
-                const uint32_t b = __ffs(bits) - 1u;
-                bits &= bits - 1u;
-                st_relaxed(&c.dirty[wq * 32u + b], 1u);
+        myclaim = warp_sum(myclaim);
+        if (lane == 0 && myclaim) atomicAdd(&sc.nclaim, myclaim);
+        __syncthreads();
+        te = block_scan_excl(sm.sel_pref, nsel, sm.wsum);
+        if (tid == 0) sm.sel_pref[nsel] = te;
+        __syncthreads();
+
+        // ---- E: relax all out-edges, edge-parallel.  Each thread keeps
+        // EDGE_BATCH independent edges in flight: all CSR loads, then all
+        // read-first filters, then all atomics, so their latencies overlap.
+        uint32_t lact = 0, bad = 0;
+        for (uint32_t k0 = tid; k0 < te; k0 += EDGE_BATCH * T) {
+            uint32_t vv[EDGE_BATCH], cc[EDGE_BATCH], aa[EDGE_BATCH];
+            uint32_t a = 0;
+#pragma unroll
+            for (int j = 0; j < EDGE_BATCH; ++j) {
+                const uint32_t k = k0 + (uint32_t)j * T;
+                vv[j] = NONE;
+                if (k < te) {
+                    uint32_t b = nsel;  // sel_pref[a] <= k < sel_pref[b]; a only grows with k
+                    while (b - a > 1u) {
+                        const uint32_t m = (a + b) >> 1;
+                        if (sm.sel_pref[m] <= k)
+                            a = m;
+                        else
+                            b = m;
+                    }
+                    const uint32_t e = sm.list_v[a] + (k - sm.sel_pref[a]);
+                    aa[j] = a;
+                    vv[j] = __ldg(&c.col[e]);
+                    cc[j] = __ldg(&c.w[e]);  // the weight, until it becomes the candidate below
+                }
+            }
+            unsigned long long cur[EDGE_BATCH];
+#pragma unroll
+            for (int j = 0; j < EDGE_BATCH; ++j) {
+                cur[j] = 0;
+                if (vv[j] == NONE) continue;
+                if (!W::weight_ok(cc[j]) || vv[j] >= c.V) {
+                    bad |= 1u;
+                    vv[j] = NONE;
+                    continue;
+                }
+                if (!W::add(sm.list_d[aa[j]], cc[j], cc[j])) {
+                    bad |= 2u;
+                    vv[j] = NONE;
+                    continue;
+                }
+                // read-first filter: a stale (higher) value only lets a useless atomic through
+                cur[j] = __ldcg(&c.packed[vv[j]]);
+            }
+            uint32_t improved = 0;
+#pragma unroll
+            for (int j = 0; j < EDGE_BATCH; ++j) {
+                if (vv[j] == NONE) continue;
+                const unsigned long long key = ((unsigned long long)cc[j] << 32) | sm.sel_v[aa[j]];
+                if (key < cur[j]) {
+                    ++cnt.atomics;
+                    const unsigned long long old = atomicMin(&c.packed[vv[j]], key);
+                    if (key < old && (uint32_t)(old >> 32) > cc[j]) improved |= 1u << j;
+                }
+            }
+            if (improved) {
+                // every lowered word before any of this thread's inbox bits (release)
+                __threadfence();
+#pragma unroll
+                for (int j = 0; j < EDGE_BATCH; ++j) {
+                    if (!(improved & (1u << j))) continue;
+                    const uint32_t v = vv[j];
+                    ++cnt.improved;
+                    const uint32_t bit = 1u << (v & 31u);
+                    const uint32_t ob = atomicOr(&c.bitmap[v >> 5], bit);
+                    if (!(ob & bit)) {
+                        ++lact;
+                        if (STATIC) {
+                            const uint32_t p = v / c.B;
+                            const uint32_t q = p * c.split + (v - p * c.B) / c.Bq;
+                            if (q != my_q) ++cnt.remote;
+                            atomicOr(&sm.touched[q >> 5], 1u << (q & 31u));
+                        }
+                    }
+                }
             }
         }
-        if (tid == 0 && found > sc.nclaim) st_relaxed(&c.dirty[my_q], 1u);  // more left in this unit
+        lact = warp_sum(lact);
+        bad = __reduce_or_sync(0xFFFFFFFFu, bad);
+        if (lane == 0) {
+            if (lact) atomicAdd(&sc.act, lact);
+            if (bad) atomicOr(&sc.bad, bad);
+        }
+        __syncthreads();
+    }
+
+    // ---- F: settle the count, ring doorbells (warp 0)
+    if (tid < 32) {
+        if (STATIC) {
+            if (tid == 0) {
+                const unsigned long long d =
+                    (unsigned long long)sc.act - ROUND_RESERVE - (unsigned long long)sc.nclaim;
+                atomicAdd(&c.hdr->pending, d);  // two's complement: adds act, returns reserve and takes
+            }
+            __threadfence();  // new bits (set before the barrier above) before the doorbells
+            for (uint32_t wq = tid; wq < c.Qw; wq += 32u) {
+                uint32_t bits = sm.touched[wq];
+                if (!bits) continue;
+                sm.touched[wq] = 0;
+                while (bits) {
+                    const uint32_t b = __ffs(bits) - 1u;
+                    bits &= bits - 1u;
+                    st_relaxed(&c.dirty[wq * 32u + b], 1u);
+                }
+            }
+            if (tid == 0 && found > sc.nclaim) st_relaxed(&c.dirty[my_q], 1u);  // more left in this unit
+        }
+        if (tid == 0 && found) {
+            cnt.edges += te;
+            cnt.rounds += 1;
+            cnt.verts += sc.nclaim;
+            cnt.acts += sc.act;
+            if (sc.bad & 1u) set_status(c.hdr, SSSP_EINVAL);
+            if (sc.bad & 2u) set_status(c.hdr, SSSP_EOVERFLOW);
+        }
     }
     __syncthreads();
     return found;
@@ -365,9 +403,10 @@ __device__ Smem carve(uint32_t* dsm, uint32_t tile, uint32_t Qw, uint32_t* wsum,
 __device__ void flush_counters(WsHeader* h, const Counters& c) {
     // counters accumulated per thread (atomics/improved/remote) or by thread 0 (the rest)
     // stats order follows sssp_stats
-    const unsigned long long v[7] = {c.edges, c.atomics, c.improved, c.acts, c.rounds, c.verts, c.remote};
+    const unsigned long long v[8] = {c.edges, c.atomics, c.improved, c.acts, c.rounds, c.verts, c.remote,
+                                     c.idle_ns / 1000ull};
 #pragma unroll
-    for (int i = 0; i < 7; ++i) {
+    for (int i = 0; i < 8; ++i) {
         const unsigned long long x = warp_sum64(v[i]);
         if ((threadIdx.x & 31u) == 0 && x) atomicAdd(&h->stats[i], x);
     }
@@ -469,10 +508,12 @@ __global__ void __launch_bounds__(1024) k_solve(SolveLaunch L) {
                 }
                 if (pick >= 0) {
                     __threadfence();  // doorbell before the inbox scan
+                    if (idle_start) cnt.idle_ns += globaltimer_ns() - idle_start;
                     idle_start = 0;
                     backoff = 32;
                 } else if (ld_relaxed(&L.hdr->pending) == 0ull) {
                     pick = -2;  // nothing queued, nothing in flight: terminated
+                    if (idle_start) cnt.idle_ns += globaltimer_ns() - idle_start;
                 } else {
                     const uint64_t now = globaltimer_ns();
                     if (idle_start == 0) {
