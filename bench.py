@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--scale", type=int, default=22)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--extras", action="store_true", help="also time batched and differentiable workloads")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched, differentiable and grid workloads")
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--delta", type=float, default=0.0)
     ap.add_argument("--threads", type=int, default=0)
@@ -262,7 +262,7 @@ def run_ours(a):
         "work": {"reached_edges": E_r, "reached_vertices": V_r, "stats_last_step": stats,
                  "work_inflation": round(stats["edges_scanned"] / max(E_r, 1), 4)},
     }
-    if a.extras and rank == 0:
+    if not a.no_extras and rank == 0:
         line["extras"] = extras(sssp, dev)
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -363,8 +363,104 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+def _evt():
+    import torch
+    return torch.cuda.Event(enable_timing=True)
+
+
+def _time_ms(fn, reps):
+    import torch
+    a, b = _evt(), _evt()
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def extras_batched(sssp, dev):
+    """512 graphs x 16 sources: one CUDA-graph replay of the batched kernel vs per-problem sssp_solve
+    launches (one source each) and per-graph launches (16 sources each), same options."""
+    import torch
+    graphs0, sources = gg.workload_batch512()
+    # the per-solve baseline gets a partition count that spreads one graph over many blocks
+    graphs = [sssp.build_csr(g.V, g.src, g.dst, g.w, partitions=max(1, min(148, g.V // 512))) for g in graphs0]
+    del graphs0
+    n_prob = sum(len(s) for s in sources)
+    edges = sum(g.E for g in graphs)
+    b = sssp.Batch(graphs, sources)
+    b.make_plan()
+    b.replay()
+    st, stats = b.status()
+    assert st == sssp.SSSP_OK, sssp.status_string(st)
+    ms_plan = _time_ms(b.replay, 3)
+    # per-graph launches (16 sources in one sssp_solve each)
+    solvers = [(sssp.Solver(g, len(s)), torch.from_numpy(s.view(np.int32)).to(dev)) for g, s in zip(graphs, sources)]
+    ms_graph = _time_ms(lambda: [sv.launch(src) for sv, src in solvers], 1)
+    # per-problem launches (one source per sssp_solve)
+    one = [(sssp.Solver(g, 1), torch.from_numpy(s.view(np.int32)).to(dev)) for g, s in zip(graphs, sources)]
+
+    def per_problem():
+        for sv, src in one:
+            for i in range(src.numel()):
+                sv.launch(src[i:i + 1])
+    ms_prob = _time_ms(per_problem, 1)
+    return {"workload": "512 graphs (ER deg 8 / R-MAT ef 8, n = 2^U(10,17)), 16 sources each",
+            "problems": n_prob, "edges_total": int(edges),
+            "graph_replay_ms": round(ms_plan, 3), "solves_per_s": round(n_prob / ms_plan * 1e3, 1),
+            "per_graph_launches_ms": round(ms_graph, 3), "per_problem_launches_ms": round(ms_prob, 3),
+            "speedup_vs_per_problem": round(ms_prob / ms_plan, 3),
+            "speedup_vs_per_graph": round(ms_graph / ms_plan, 3)}
+
+
+def extras_differentiable(sssp, dev):
+    """R-MAT scale 18, fp32 weights, 32 sources: forward solve, backward, forward+backward."""
+    import torch
+    g0, srcs, gup = gg.workload_rmat18_f32()
+    g = sssp.build_csr(g0.V, g0.src, g0.dst, g0.w, partitions=8)
+    solver = sssp.Solver(g, len(srcs))
+    src_d = torch.from_numpy(srcs.view(np.int32)).to(dev)
+    gup_d = torch.from_numpy(gup).to(dev)
+    solver.launch(src_d)
+    st, _ = solver.status()
+    assert st == sssp.SSSP_OK
+    ms_fwd = _time_ms(lambda: solver.launch(src_d), 5)
+    ms_bwd = _time_ms(lambda: sssp.backward(g, solver.pred, gup_d), 5)
+    ms_both = _time_ms(lambda: (solver.launch(src_d), sssp.backward(g, solver.pred, gup_d)), 5)
+    return {"workload": "rmat-s18-ef8 fp32 weights, 32 sources", "forward_ms": round(ms_fwd, 3),
+            "backward_ms": round(ms_bwd, 3), "forward_backward_ms": round(ms_both, 3),
+            "fwd_bwd_over_fwd": round(ms_both / ms_fwd, 3)}
+
+
+def extras_grid(sssp, dev, delta=2048.0):
+    """4096 x 4096 grid, corner source: the high-diameter case."""
+    import torch
+    g0, srcs, P = gg.workload_grid4096()
+    g = sssp.build_csr(g0.V, g0.src, g0.dst, g0.w, partitions=P)
+    del g0
+    solver = sssp.Solver(g, 1, sssp.options(delta=delta, tile=4096))
+    src_d = torch.from_numpy(srcs.view(np.int32)).to(dev)
+    solver.launch(src_d)
+    st, stats = solver.status()
+    assert st == sssp.SSSP_OK
+    ms = _time_ms(lambda: solver.launch(src_d), 3)
+    return {"workload": "grid 4096x4096, corner source", "delta": delta, "ms": round(ms, 3),
+            "gteps": round(g.E / (ms * 1e-3) / 1e9, 4), "rounds": stats["rounds"],
+            "work_inflation": round(stats["edges_scanned"] / g.E, 3)}
+
+
 def extras(sssp, dev):
-    return {}
+    out = {}
+    for name, fn in (("batched", extras_batched), ("differentiable", extras_differentiable), ("grid", extras_grid)):
+        t0 = time.perf_counter()
+        try:
+            out[name] = fn(sssp, dev)
+        except Exception as e:  # an extra must not hide the headline line
+            out[name] = {"error": repr(e)[:300]}
+        out[name]["wall_s"] = round(time.perf_counter() - t0, 1)
+    return out
 
 
 if __name__ == "__main__":

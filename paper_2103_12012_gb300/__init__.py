@@ -296,21 +296,30 @@ class Batch:
     """A batch of independent (graph, source) problems over several graphs, solved in one launch."""
 
     def __init__(self, graphs, sources, opts: SsspOptions | None = None):
-        """graphs: list of canonical oracle-style CSRs (objects with V, row_ptr, col, w numpy arrays);
+        """graphs: DeviceGraph objects (from build_csr) or canonical CSRs with numpy V, row_ptr, col, w;
         sources: list of source arrays, one per graph."""
         torch = _torch()
         self.opts = opts or options()
         Vs = [int(g.V) for g in graphs]
-        Es = [int(g.row_ptr[-1]) for g in graphs]
         self.row_off = np.concatenate([[0], np.cumsum([v + 1 for v in Vs])[:-1]]).astype(np.uint64)
+        if isinstance(graphs[0], DeviceGraph):
+            # device CSRs (e.g. from build_csr): concatenate on the device
+            Es = [int(g.E) for g in graphs]
+            self.row_ptr = torch.cat([g.row_ptr for g in graphs])
+            self.col = torch.cat([g.col[:g.E] for g in graphs])
+            self.w = torch.cat([g.w[:g.E] for g in graphs])
+            wt = self.wtype = graphs[0].wtype
+        else:
+            Es = [int(g.row_ptr[-1]) for g in graphs]
+            rp = np.concatenate([np.asarray(g.row_ptr, np.uint32) for g in graphs])
+            col = np.concatenate([np.asarray(g.col, np.uint32) for g in graphs])
+            wt = W_F32 if graphs[0].w.dtype == np.float32 else W_U32
+            w = np.concatenate([np.asarray(g.w) for g in graphs])
+            self.row_ptr = _as_dev_u32(rp)
+            self.col = _as_dev_u32(col)
+            self.w, self.wtype = _w_dev(w)
         self.edge_off = np.concatenate([[0], np.cumsum(Es)[:-1]]).astype(np.uint64)
-        rp = np.concatenate([np.asarray(g.row_ptr, np.uint32) for g in graphs])
-        col = np.concatenate([np.asarray(g.col, np.uint32) for g in graphs])
-        wt = W_F32 if graphs[0].w.dtype == np.float32 else W_U32
-        w = np.concatenate([np.asarray(g.w) for g in graphs])
-        self.row_ptr = _as_dev_u32(rp)
-        self.col = _as_dev_u32(col)
-        self.w, self.wtype = _w_dev(w)
+        self.Es = Es
         self.gdesc = (SsspBatchGraph * len(graphs))(*[SsspBatchGraph(int(a), int(b), v, e) for a, b, v, e in
                                                       zip(self.row_off, self.edge_off, Vs, Es)])
         pg, ps = [], []

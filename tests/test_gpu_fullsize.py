@@ -1,0 +1,169 @@
+"""Full-size workloads on the CUDA path, in the launch configuration the benchmark uses.
+
+For every workload the GPU CSR equals the oracle's, a sample of sources (or
+batch problems) is compared with the oracle's Dijkstra element by element,
+and every source is checked against properties that hold at any size: d(s)=0,
+d[v] <= d[u] + w(u,v) on every edge, every predecessor edge is tight, and the
+predecessor is the smallest-id tight in-neighbour.  Float32 distances must be
+bit-exact as well (both sides round each d(u)+w once).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def sssp():
+    import paper_2103_12012_gb300 as m
+    m.lib()
+    return m
+
+
+def u32(t):
+    return t.detach().cpu().numpy().view(np.uint32)
+
+
+def check_csr_equal(g, ref):
+    assert g.E == ref.E
+    assert np.array_equal(u32(g.row_ptr), ref.row_ptr)
+    assert np.array_equal(u32(g.col), ref.col)
+    assert np.array_equal(u32(g.w), ref.w.view(np.uint32))
+
+
+def check_invariants(g, dist, pred, sources):
+    """Properties of a shortest-path result that hold at any size (checked with torch on the device)."""
+    V = g.V
+    rp = g.row_ptr.long()
+    tail = torch.repeat_interleave(torch.arange(V, device="cuda"), rp[1:] - rp[:-1])
+    head = g.col.long()
+    f32 = g.wtype == 1
+    INF = torch.tensor(float("inf") if f32 else 0xFFFFFFFF, device="cuda", dtype=torch.float64)
+    w = g.w.double() if f32 else (g.w.long() & 0xFFFFFFFF).double()
+    for i, s in enumerate(sources):
+        d = dist[i].double() if f32 else (dist[i].long() & 0xFFFFFFFF).double()
+        p = pred[i].long() & 0xFFFFFFFF
+        assert d[s] == 0 and p[s] == 0xFFFFFFFF
+        du, dv = d[tail], d[head]
+        fin = du != INF
+        # candidate in the arithmetic of the weights: float32 sum rounded once, or exact integers
+        cand = (dist[i][tail].float() + g.w.float()).double() if f32 else du + w
+        assert bool((dv[fin] <= cand[fin]).all()), "an edge is not relaxed"
+        tight = fin & (cand == dv) & (head != s)
+        # canonical predecessor: smallest tight in-neighbour
+        best = torch.full((V,), 0xFFFFFFFF, dtype=torch.long, device="cuda")
+        best.scatter_reduce_(0, head[tight], tail[tight], reduce="amin")
+        reached = (d != INF)
+        reached[s] = False
+        assert torch.equal(p[reached], best[reached])
+        assert bool((p[~reached & (torch.arange(V, device="cuda") != s)] == 0xFFFFFFFF).all())
+
+
+def check_oracle_sources(ref, dist, pred, sources, which):
+    for i in which:
+        d, p, _ = oracle.dijkstra(ref, int(sources[i]))
+        assert np.array_equal(u32(dist[i]), d.view(np.uint32)), f"source #{i}"
+        assert np.array_equal(u32(pred[i]), p), f"source #{i}"
+
+
+def test_rmat22_eight_sources(sssp):
+    g0, srcs, P = gg.workload_rmat22()
+    ref = oracle.csr_of(g0)
+    g = sssp.build_csr(g0.V, g0.src, g0.dst, g0.w, partitions=P)
+    check_csr_equal(g, ref)
+    del g0
+    dist, pred, st, stats = sssp.solve(g, srcs)
+    assert st == sssp.SSSP_OK
+    check_oracle_sources(ref, dist, pred, srcs, [0, len(srcs) - 1])
+    check_invariants(g, dist, pred, srcs.tolist())
+
+
+def test_grid4096_corner(sssp):
+    g0, srcs, P = gg.workload_grid4096()
+    ref = oracle.csr_of(g0)
+    g = sssp.build_csr(g0.V, g0.src, g0.dst, g0.w, partitions=P)
+    check_csr_equal(g, ref)
+    del g0
+    dist, pred, st, stats = sssp.solve(g, srcs, sssp.options(delta=2048, tile=4096))
+    assert st == sssp.SSSP_OK
+    check_oracle_sources(ref, dist, pred, srcs, [0])
+    check_invariants(g, dist, pred, srcs.tolist())
+
+
+def test_er16k_prune_and_solve(sssp):
+    g0, srcs, P = gg.workload_er16k()
+    ref = oracle.csr_of(g0)
+    g = sssp.build_csr(g0.V, g0.src, g0.dst, g0.w, partitions=P)
+    check_csr_equal(g, ref)
+    for mode in (0, 1):
+        keep, wit = sssp.prune(g, mode)
+        rk, rw = oracle.trishla(ref, P, mode)
+        assert np.array_equal(keep.cpu().numpy(), rk) and np.array_equal(u32(wit), rw)
+    gp = sssp.compact(g, keep)
+    for graph in (g, gp):
+        dist, pred, st, _ = sssp.solve(graph, srcs)
+        assert st == sssp.SSSP_OK
+        check_oracle_sources(ref, dist, pred, srcs, [0])
+        check_invariants(graph, dist, pred, srcs.tolist())
+
+
+def test_rmat18_f32_forward_backward(sssp):
+    g0, srcs, gup = gg.workload_rmat18_f32()
+    ref = oracle.csr_of(g0)
+    g = sssp.build_csr(g0.V, g0.src, g0.dst, g0.w, partitions=8)
+    check_csr_equal(g, ref)
+    dist, pred, st, _ = sssp.solve(g, srcs)
+    assert st == sssp.SSSP_OK
+    rd = np.empty((len(srcs), g.V), np.float32)
+    rp = np.empty((len(srcs), g.V), np.uint32)
+    for i, s in enumerate(srcs):
+        rd[i], rp[i], _ = oracle.dijkstra(ref, int(s))
+    assert np.array_equal(u32(dist), rd.view(np.uint32))
+    assert np.array_equal(u32(pred), rp)
+    check_invariants(g, dist, pred, srcs.tolist())
+    grad = sssp.backward(g, pred, torch.from_numpy(gup).cuda()).cpu().numpy().astype(np.float64)
+    rg = oracle.tree_grad(ref, rd, rp, gup)
+    # float64 accumulation on both sides; the float32 output rounding bounds the difference
+    assert np.allclose(grad, rg, rtol=1e-6, atol=1e-6 * np.abs(rg).max())
+    assert (grad[rg == 0] == 0).all()
+
+
+def test_batch512_sampled(sssp):
+    graphs0, sources = gg.workload_batch512()
+    graphs = [oracle.csr_of(g) for g in graphs0]
+    del graphs0
+    b = sssp.Batch(graphs, sources)
+    b.make_plan()
+    b.replay()
+    st, stats = b.status()
+    assert st == sssp.SSSP_OK
+    assert b.n_problems == sum(len(s) for s in sources) == 512 * 16
+    rng = np.random.default_rng(7)
+    for i in rng.choice(b.n_problems, 96, replace=False):
+        gi, s = int(b.prob_graph[i]), int(b.prob_source[i])
+        d, p, _ = oracle.dijkstra(graphs[gi], s)
+        bd, bp = b.result(i)
+        assert np.array_equal(u32(bd), d) and np.array_equal(u32(bp), p), (i, gi, s)
+    # every problem: d(s) = 0 and the predecessor of each reached vertex is tight (vectorised per graph)
+    for i in range(0, b.n_problems, 97):
+        gi, s = int(b.prob_graph[i]), int(b.prob_source[i])
+        bd, bp = b.result(i)
+        d = u32(bd).astype(np.int64)
+        p = u32(bp).astype(np.int64)
+        assert d[s] == 0
+        G = graphs[gi]
+        reached = (d != 0xFFFFFFFF)
+        reached[s] = False
+        vs = np.nonzero(reached)[0]
+        for v in vs[:200]:
+            u = p[v]
+            lo, hi = G.row_ptr[u], G.row_ptr[u + 1]
+            k = lo + np.searchsorted(G.col[lo:hi], v)
+            assert G.col[k] == v and d[u] + int(G.w[k]) == d[v]
