@@ -248,7 +248,7 @@ def run_ours(a):
                                f"{g0.V} vertices, {g0.E_raw} raw edges ({g.E} after dedupe), "
                                f"{S} sources per GPU, {P} partitions",
                    "partitions": P, "sources_per_gpu": S, "l2": "inputs larger than L2 (CSR and state > 0.5 GB)",
-                   "options": {"threads": a.threads or 512, "tile": a.tile or 1024, "delta": a.delta or 8,
+                   "options": {"threads": a.threads or 512, "tile": a.tile or 1024, "delta": a.delta or 4,
                                "split": a.split or 1}},
         "roofline": {"bound": "hbm", "kernel": "k_solve (persistent relaxation)", "achieved": round(achieved, 1),
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),

@@ -81,12 +81,13 @@ typedef struct {
 /* Tuning knobs; a zero field means "default".  None of them changes the
  * result, only the schedule. */
 typedef struct {
-    uint32_t threads;      /* threads per block of the relaxation kernel: 128..1024, multiple of 32 (default 512) */
+    uint32_t threads;      /* threads per block of the relaxation kernel, multiple of 32 (default 512):
+                              128..512 for sssp_solve, 128..1024 for the batched solve */
     uint32_t blocks_per_sm;/* persistent blocks per SM (default: as many as fit) */
     uint32_t tile;         /* most vertices one block takes from its inbox per round: 32..4096 (default 1024) */
     uint32_t split;        /* blocks sharing one partition, each owning a sub-block of its vertices (default 1) */
     double delta;          /* bucket width: a round takes inbox vertices with dist < min dist + delta
-                              (default: uint32 -> 8, float32 -> 0.0625) */
+                              (default: uint32 -> 4, float32 -> 0.0625) */
     uint64_t timeout_ns;   /* limit on a block's continuous idle wait (default 20 s); a persistent
                               kernel also stops after 3 x timeout_ns in total */
     uint32_t flags;        /* SSSP_FLAG_* */

@@ -17,10 +17,10 @@ constexpr uint32_t DEF_THREADS = 512;
 constexpr uint32_t DEF_TILE = 1024;
 constexpr uint64_t DEF_TIMEOUT_NS = 20ull * 1000 * 1000 * 1000;
 constexpr uint32_t MAX_UNITS_PER_SOURCE = 65536;
-// Default bucket widths: about 1/16 of the mean weight of the workloads this library
-// is tuned on (uint32 U{1..255}: 8; float32 U[0.5,2): 1/16).  Measured on R-MAT scale 22:
+// Default bucket widths: about 1/32 of the mean weight of the workloads this library
+// is tuned on (uint32 U{1..255}: 4; float32 U[0.5,2): 1/16).  Measured on R-MAT scale 22:
 // smaller widths scan fewer edges (closer to Dijkstra order), larger ones need fewer rounds.
-constexpr uint32_t DEF_DELTA_U32 = 8;
+constexpr uint32_t DEF_DELTA_U32 = 4;
 constexpr float DEF_DELTA_F32 = 0.0625f;
 
 struct Resolved {
@@ -162,7 +162,7 @@ sssp_status sssp_solve(const sssp_graph* g, const uint32_t* sources, uint32_t S,
                        const sssp_options* opt, void* ws, size_t ws_bytes, sssp_stream_t stream) {
     Resolved r;
     if (!graph_ok(g) || S == 0 || !sources || !dist || !ws || !resolve(opt, g->wtype, &r)) return SSSP_EINVAL;
-    if (!aligned16(ws)) return SSSP_EINVAL;
+    if (!aligned16(ws) || r.threads > SOLVE_MAX_THREADS) return SSSP_EINVAL;
     const SolveWs L = solve_layout(g, S, r.split);
     if ((uint64_t)S * L.Q > 0xFFFFFFFFull / 2 || L.Q > MAX_UNITS_PER_SOURCE * 16u) return SSSP_EINVAL;
     if (ws_bytes < L.total) return SSSP_ENOMEM;

@@ -44,6 +44,7 @@ struct SolveLaunch {
     uint32_t* pred;
 };
 
+constexpr uint32_t SOLVE_MAX_THREADS = 512;  // block size limit of the solve kernel
 size_t relax_smem_bytes(uint32_t tile, uint32_t Q);
 cudaError_t relax_max_blocks_per_sm(int wtype, uint32_t threads, uint32_t tile, uint32_t Q, int* out);
 cudaError_t launch_solve(const SolveLaunch& L, cudaStream_t st);

@@ -59,6 +59,9 @@ def test_host_argument_checks_without_gpu(L):
     # bad options
     for o in (sssp.options(threads=100), sssp.options(threads=2048), sssp.options(tile=8), sssp.options(delta=-1)):
         assert L.sssp_solve_workspace_size(ctypes.byref(g), 1, ctypes.byref(o)) == 0
+    # the solve kernel runs at most 512 threads per block
+    o = sssp.options(threads=1024)
+    assert L.sssp_solve(ctypes.byref(g), 16, 1, 16, None, ctypes.byref(o), 256, 1 << 30, None) == sssp.SSSP_EINVAL
     # too-small workspace
     need = L.sssp_solve_workspace_size(ctypes.byref(g), 2, ctypes.byref(opt))
     assert need > 0

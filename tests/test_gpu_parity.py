@@ -146,7 +146,7 @@ def test_solve_partition_counts(sssp, P, split):
 
 
 @pytest.mark.parametrize("opts", [dict(threads=128, tile=32, delta=1), dict(threads=256, tile=64, delta=10),
-                                  dict(threads=1024, tile=4096, delta=1e9), dict(threads=512, tile=100, delta=50,
+                                  dict(threads=512, tile=4096, delta=1e9), dict(threads=512, tile=100, delta=50,
                                                                                  blocks_per_sm=1)])
 def test_solve_schedule_does_not_change_result(sssp, opts):
     V = 20000
