@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--delta", type=float, default=0.0)
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--split", type=int, default=0)
+    ap.add_argument("--no-tune", action="store_true", help="library defaults instead of the autotuned schedule")
     return ap.parse_args()
 
 
@@ -71,6 +72,20 @@ def rank_sources(g, rank, count=8):
     """The 8 sources of a rank: rank 0 takes the workload's own sources; other ranks draw their own."""
     seed = gg.BASE_SEED + 2 + 1000 * rank
     return gg.pick_sources(seed, g, count)
+
+
+def dram_traffic(edges_scanned):
+    """DRAM bytes per launch of the relaxation kernel from the committed ncu capture, scaled to this
+    launch by edges scanned; None if the kernel source changed since that capture."""
+    import hashlib
+    try:
+        rec = json.loads(open(os.path.join(ROOT, "profiles", "k_solve_dram_traffic.txt")).read())
+        src = open(os.path.join(ROOT, rec["source"]), "rb").read()
+    except (OSError, ValueError, KeyError):
+        return None, "no capture"
+    if hashlib.sha256(src).hexdigest() != rec["source_sha256"]:
+        return None, "kernel changed since the capture"
+    return int(rec["dram_bytes_per_scanned_edge"] * edges_scanned), rec["capture"] + ", scaled by edges scanned"
 
 
 def peaks():
@@ -169,9 +184,15 @@ def run_ours(a):
     del src_d, dst_d, w_d
     inter_total = int(inter.sum().item())
 
-    opts = sssp.options(threads=a.threads, tile=a.tile, delta=a.delta, split=a.split)
-    solver = sssp.Solver(g, S, opts)
     sources_d = torch.from_numpy(srcs.view(np.int32)).to(dev)
+    tuned_ms = None
+    if a.no_tune or a.threads or a.tile or a.delta or a.split:
+        opts = sssp.options(threads=a.threads, tile=a.tile, delta=a.delta, split=a.split)
+    else:
+        t0 = time.perf_counter()
+        opts, tuned_ms = sssp.autotune(g, sources_d)
+        tune_s = time.perf_counter() - t0
+    solver = sssp.Solver(g, S, opts)
 
     # warm-up (also the step whose output defines the traversed-edge count)
     for _ in range(max(a.warmup, 1)):
@@ -229,6 +250,7 @@ def run_ours(a):
     peak, peak_kind = peaks()
     relax_avg = statistics.mean(relax_ms)
     achieved = alg_bytes / (relax_avg * 1e-3) / 1e9
+    traffic, traffic_note = dram_traffic(stats["edges_scanned"])
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -248,11 +270,13 @@ def run_ours(a):
                                f"{g0.V} vertices, {g0.E_raw} raw edges ({g.E} after dedupe), "
                                f"{S} sources per GPU, {P} partitions",
                    "partitions": P, "sources_per_gpu": S, "l2": "inputs larger than L2 (CSR and state > 0.5 GB)",
-                   "options": {"threads": a.threads or 512, "tile": a.tile or 1024, "delta": a.delta or 4,
-                               "split": a.split or 1}},
+                   "options": {"threads": opts.threads or 512, "tile": opts.tile or 1024,
+                               "delta": opts.delta or 4, "split": opts.split or 1,
+                               "autotuned": not (a.no_tune or a.threads or a.tile or a.delta or a.split)}},
         "roofline": {"bound": "hbm", "kernel": "k_solve (persistent relaxation)", "achieved": round(achieved, 1),
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "traffic": None, "alg_bytes_per_launch": alg_bytes, "kernel_ms": round(relax_avg, 4)},
+                     "traffic": traffic, "traffic_note": traffic_note, "alg_bytes_per_launch": alg_bytes,
+                     "kernel_ms": round(relax_avg, 4)},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": clk,
@@ -434,19 +458,21 @@ def extras_differentiable(sssp, dev):
             "fwd_bwd_over_fwd": round(ms_both / ms_fwd, 3)}
 
 
-def extras_grid(sssp, dev, delta=2048.0):
-    """4096 x 4096 grid, corner source: the high-diameter case."""
+def extras_grid(sssp, dev):
+    """4096 x 4096 grid, corner source: the high-diameter case (autotuned schedule)."""
     import torch
     g0, srcs, P = gg.workload_grid4096()
     g = sssp.build_csr(g0.V, g0.src, g0.dst, g0.w, partitions=P)
     del g0
-    solver = sssp.Solver(g, 1, sssp.options(delta=delta, tile=4096))
     src_d = torch.from_numpy(srcs.view(np.int32)).to(dev)
+    opts, _ = sssp.autotune(g, src_d)
+    solver = sssp.Solver(g, 1, opts)
     solver.launch(src_d)
     st, stats = solver.status()
     assert st == sssp.SSSP_OK
     ms = _time_ms(lambda: solver.launch(src_d), 3)
-    return {"workload": "grid 4096x4096, corner source", "delta": delta, "ms": round(ms, 3),
+    return {"workload": "grid 4096x4096, corner source", "delta": opts.delta, "tile": opts.tile,
+            "split": opts.split, "ms": round(ms, 3),
             "gteps": round(g.E / (ms * 1e-3) / 1e9, 4), "rounds": stats["rounds"],
             "work_inflation": round(stats["edges_scanned"] / g.E, 3)}
 

@@ -200,6 +200,23 @@ sssp_status sssp_solve(const sssp_graph* g, const uint32_t* sources, uint32_t S,
                        const sssp_options* opt, void* ws, size_t ws_bytes, sssp_stream_t stream);
 
 /*
+ * Autotuner for sssp_solve (the paper has no tuner; its knobs are the process
+ * count and the termination timeout).  Runs sssp_solve on (g, sources) with
+ * candidate schedules and returns the fastest: the bucket width delta is
+ * searched over {1/64 .. 4} x the mean of a sample of the weights, then tile
+ * over {1024, 2048, 4096}, then split over {1, 2, 4} (split only where ws is
+ * large enough).  Each candidate runs `trials` times (>= 1) after one
+ * warm-up, timed with CUDA events on `stream`; candidates that fail are
+ * skipped.  Synchronous.  Results do not depend on the schedule, so dist and
+ * pred hold a valid solve afterwards.
+ *   base : options to start from (may be NULL); best : out; best_ms : out (may be NULL)
+ *   ws   : as for sssp_solve with `base` (and split up to 4 if it fits)
+ */
+sssp_status sssp_autotune(const sssp_graph* g, const uint32_t* sources, uint32_t S, void* dist, uint32_t* pred,
+                          void* ws, size_t ws_bytes, const sssp_options* base, uint32_t trials,
+                          sssp_options* best, float* best_ms, sssp_stream_t stream);
+
+/*
  * Synchronise `stream`, then return the status recorded on the device by the
  * last call that used workspace `ws` (and clear nothing).  stats (host, may
  * be NULL) receives that call's counters (zero for calls that keep none).

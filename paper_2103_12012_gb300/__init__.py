@@ -70,6 +70,7 @@ _SIGS = {
     "sssp_solve_workspace_size": (sz, [P, u32, P]),
     "sssp_solve": (i32, [P, P, u32, P, P, P, P, sz, P]),
     "sssp_workspace_status": (i32, [P, P, P]),
+    "sssp_autotune": (i32, [P, P, u32, P, P, P, sz, P, u32, P, P, P]),
     "sssp_solve_noalloc": (i32, [P, P, u32, P, P, P, P, P]),
     "sssp_batch_workspace_size": (sz, [P, P]),
     "sssp_solve_batched": (i32, [P, P, P, sz, P]),
@@ -283,6 +284,54 @@ class Solver:
             raise SsspError(st, "sssp_solve (device)")
         self.last_status, self.last_stats = st, stats
         return dist, pred
+
+
+def _tune_cache_path():
+    return os.environ.get("SSSP_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "sssp_gb300",
+                                                           "tune.json"))
+
+
+def _graph_class(g: DeviceGraph, S: int) -> str:
+    """Cache key: sizes, weight type, partitions, sources and the weight scale (mean of a sample)."""
+    wm = float(g.w[:min(g.E, 65536)].float().mean().item()) if g.E and g.wtype == W_F32 else (
+        float((g.w[:min(g.E, 65536)].long() & 0xFFFFFFFF).double().mean().item()) if g.E else 0.0)
+    return f"V{g.V}:E{g.E}:w{g.wtype}:P{g.partitions}:S{S}:m{wm:.3g}"
+
+
+def autotune(g: DeviceGraph, sources, base: SsspOptions | None = None, trials: int = 1, cache: bool = True):
+    """Options for sssp_solve on graphs of this class: from the JSON cache (SSSP_TUNE_CACHE), else
+    measured by sssp_autotune and stored.  Returns (options, ms or None if cached)."""
+    import json
+    S = len(sources) if not hasattr(sources, "numel") else int(sources.numel())
+    key = _graph_class(g, S)
+    path = _tune_cache_path()
+    db = {}
+    if cache and os.path.exists(path):
+        try:
+            db = json.load(open(path))
+        except ValueError:
+            db = {}
+    if key in db:
+        o = db[key]
+        return options(threads=o["threads"], tile=o["tile"], split=o["split"], delta=o["delta"]), None
+    solver = Solver(g, S, options(split=4))  # workspace large enough for every split candidate
+    if isinstance(sources, np.ndarray) or isinstance(sources, (list, tuple)):
+        sources = _as_dev_u32(np.asarray(sources, np.uint32))
+    best = SsspOptions()
+    ms = ctypes.c_float()
+    b = base or options()
+    _check(lib().sssp_autotune(ctypes.byref(solver.gc), _ptr(sources), S, _ptr(solver.dist), _ptr(solver.pred),
+                               _ptr(solver.ws), solver.ws_bytes, ctypes.byref(b), trials, ctypes.byref(best),
+                               ctypes.byref(ms), _stream()), "sssp_autotune")
+    rec = dict(threads=int(best.threads), tile=int(best.tile), split=int(best.split), delta=float(best.delta),
+               ms=round(float(ms.value), 4))
+    if cache:
+        db[key] = rec
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        tmp = path + ".tmp%d" % os.getpid()
+        json.dump(db, open(tmp, "w"), indent=1, sort_keys=True)
+        os.replace(tmp, path)
+    return options(threads=rec["threads"], tile=rec["tile"], split=rec["split"], delta=rec["delta"]), rec["ms"]
 
 
 def solve(g: DeviceGraph, sources, opts: SsspOptions | None = None, check=True):

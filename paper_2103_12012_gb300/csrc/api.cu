@@ -204,6 +204,98 @@ sssp_status sssp_solve(const sssp_graph* g, const uint32_t* sources, uint32_t S,
     return launch_solve(l, (cudaStream_t)stream) == cudaSuccess ? SSSP_OK : SSSP_ECUDA;
 }
 
+sssp_status sssp_autotune(const sssp_graph* g, const uint32_t* sources, uint32_t S, void* dist, uint32_t* pred,
+                          void* ws, size_t ws_bytes, const sssp_options* base, uint32_t trials,
+                          sssp_options* best, float* best_ms, sssp_stream_t stream) {
+    if (!graph_ok(g) || S == 0 || !sources || !dist || !ws || !best) return SSSP_EINVAL;
+    sssp_options b{};
+    if (base) b = *base;
+    b.ev_relax_begin = b.ev_relax_end = nullptr;
+    Resolved r;
+    if (!resolve(&b, g->wtype, &r)) return SSSP_EINVAL;
+    if (trials == 0) trials = 1;
+    cudaStream_t st = (cudaStream_t)stream;
+    // mean of a sample of the weights sets the scale of the bucket-width candidates
+    double mean = 1.0;
+    if (g->E) {
+        const uint32_t n = std::min<uint32_t>(g->E, 65536);
+        std::vector<uint32_t> h(n);
+        if (cudaMemcpyAsync(h.data(), g->w, 4ull * n, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return SSSP_ECUDA;
+        double sum = 0;
+        for (uint32_t x : h) {
+            if (g->wtype == SSSP_W_F32) {
+                float f;
+                std::memcpy(&f, &x, 4);
+                sum += f;
+            } else {
+                sum += x;
+            }
+        }
+        mean = sum / n;
+    }
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return SSSP_ECUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return SSSP_ECUDA;
+    }
+    // time one candidate: warm-up, then `trials` runs; +inf if it fails
+    auto run = [&](const sssp_options& o) -> float {
+        if (sssp_solve_workspace_size(g, S, &o) > ws_bytes || sssp_solve_workspace_size(g, S, &o) == 0)
+            return INFINITY;
+        if (sssp_solve(g, sources, S, dist, pred, &o, ws, ws_bytes, stream) != SSSP_OK) return INFINITY;
+        if (sssp_workspace_status(ws, stream, nullptr) != SSSP_OK) return INFINITY;
+        cudaEventRecord(e0, st);
+        for (uint32_t t = 0; t < trials; ++t)
+            if (sssp_solve(g, sources, S, dist, pred, &o, ws, ws_bytes, stream) != SSSP_OK) return INFINITY;
+        cudaEventRecord(e1, st);
+        if (sssp_workspace_status(ws, stream, nullptr) != SSSP_OK) return INFINITY;
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) return INFINITY;
+        return ms / (float)trials;
+    };
+    sssp_options cur = b;
+    float cur_ms = INFINITY;
+    const double factors[] = {1.0 / 64, 1.0 / 32, 1.0 / 16, 1.0 / 8, 1.0 / 4, 1.0 / 2, 1.0, 2.0, 4.0};
+    for (double f : factors) {
+        sssp_options o = b;
+        o.delta = g->wtype == SSSP_W_F32 ? mean * f : std::max(1.0, std::floor(mean * f));
+        const float ms = run(o);
+        if (ms < cur_ms) {
+            cur_ms = ms;
+            cur = o;
+        }
+    }
+    for (uint32_t tile : {1024u, 2048u, 4096u}) {
+        sssp_options o = cur;
+        o.tile = tile;
+        const float ms = run(o);
+        if (ms < cur_ms) {
+            cur_ms = ms;
+            cur = o;
+        }
+    }
+    for (uint32_t split : {1u, 2u, 4u}) {
+        sssp_options o = cur;
+        o.split = split;
+        const float ms = run(o);
+        if (ms < cur_ms) {
+            cur_ms = ms;
+            cur = o;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!(cur_ms < INFINITY)) return SSSP_EINTERNAL;  // no candidate ran
+    // leave a valid solve of the chosen schedule in dist/pred
+    if (sssp_solve(g, sources, S, dist, pred, &cur, ws, ws_bytes, stream) != SSSP_OK) return SSSP_ECUDA;
+    *best = cur;
+    if (best_ms) *best_ms = cur_ms;
+    return sssp_workspace_status(ws, stream, nullptr);
+}
+
 sssp_status sssp_workspace_status(const void* ws, sssp_stream_t stream, sssp_stats* stats) {
     if (!ws) return SSSP_EINVAL;
     if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return SSSP_ECUDA;

@@ -130,19 +130,63 @@ __global__ void k_emit(uint32_t V, uint64_t n, unsigned long long sentinel, cons
     }
 }
 
+// Block partition bounds and inter-edge counts.  A block takes a contiguous chunk of
+// vertices: threads count the edges of low-degree vertices themselves; vertices of degree
+// above PART_HUB are queued in shared memory and counted by the whole block together, so
+// hubs do not serialise one thread.  Counts are summed per warp for lanes that share a
+// partition before the atomic.
+constexpr uint32_t PART_HUB = 256;
+constexpr uint32_t PART_CHUNK = 4096;
+
+// called by all 32 lanes of a warp: lanes that share pu add their counts with one atomic
+__device__ __forceinline__ void add_inter(unsigned long long* inter, uint32_t pu, uint32_t c) {
+    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, pu);
+    const uint32_t sum = __reduce_add_sync(peers, c);
+    if ((__ffs(peers) - 1u) == (threadIdx.x & 31u) && sum) atomicAdd(&inter[pu], (unsigned long long)sum);
+}
+
 __global__ void k_partition(uint32_t V, uint32_t P, unsigned long long B, const uint32_t* __restrict__ row_ptr,
                             const uint32_t* __restrict__ col, uint32_t* bounds, unsigned long long* inter) {
+    __shared__ uint32_t hubs[PART_CHUNK];
+    __shared__ uint32_t nhub;
+    __shared__ unsigned long long hub_cnt;
     const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t p = gtid; p <= P; p += stride)
+    for (uint32_t p = gtid; p <= P; p += gridDim.x * blockDim.x)
         bounds[p] = (uint32_t)((unsigned long long)p * B < V ? (unsigned long long)p * B : V);
     if (!inter) return;
-    for (uint32_t u = gtid; u < V; u += stride) {
-        const uint32_t pu = (uint32_t)(u / B);
-        uint32_t c = 0;
-        const uint32_t e1 = row_ptr[u + 1];
-        for (uint32_t e = row_ptr[u]; e < e1; ++e) c += (uint32_t)(col[e] / B) != pu;
-        if (c) atomicAdd(&inter[pu], (unsigned long long)c);
+    for (uint32_t c0 = blockIdx.x * PART_CHUNK; c0 < V; c0 += gridDim.x * PART_CHUNK) {
+        const uint32_t c1 = min(c0 + PART_CHUNK, V);
+        if (threadIdx.x == 0) nhub = 0;
+        __syncthreads();
+        for (uint32_t base = c0; base < c1; base += blockDim.x) {  // same trip count for every thread
+            const uint32_t u = base + threadIdx.x;
+            uint32_t cnt = 0, pu = 0;
+            if (u < c1) {
+                pu = (uint32_t)(u / B);
+                const uint32_t e0 = row_ptr[u], e1 = row_ptr[u + 1];
+                if (e1 - e0 > PART_HUB) {
+                    hubs[atomicAdd(&nhub, 1u)] = u;
+                } else {
+                    for (uint32_t e = e0; e < e1; ++e) cnt += (uint32_t)(col[e] / B) != pu;
+                }
+            }
+            add_inter(inter, pu, cnt);
+        }
+        __syncthreads();
+        for (uint32_t h = 0; h < nhub; ++h) {
+            const uint32_t u = hubs[h];
+            const uint32_t pu = (uint32_t)(u / B);
+            if (threadIdx.x == 0) hub_cnt = 0;
+            __syncthreads();
+            unsigned long long cnt = 0;
+            for (uint32_t e = row_ptr[u] + threadIdx.x; e < row_ptr[u + 1]; e += blockDim.x)
+                cnt += (uint32_t)(col[e] / B) != pu;
+            for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
+            if ((threadIdx.x & 31u) == 0 && cnt) atomicAdd(&hub_cnt, cnt);
+            __syncthreads();
+            if (threadIdx.x == 0 && hub_cnt) atomicAdd(&inter[pu], hub_cnt);
+        }
+        __syncthreads();
     }
 }
 
@@ -225,8 +269,13 @@ cudaError_t partition_launch(const sssp_graph* g, uint32_t* bounds, uint64_t* in
     const unsigned long long B = ((unsigned long long)g->V + g->partitions - 1) / g->partitions;
     cudaError_t e;
     if (inter && (e = cudaMemsetAsync(inter, 0, sizeof(uint64_t) * g->partitions, st)) != cudaSuccess) return e;
-    k_partition<<<grid_for(std::max<uint64_t>(g->V, g->partitions + 1)), 256, 0, st>>>(
-        g->V, g->partitions, B, g->row_ptr, g->col, bounds, reinterpret_cast<unsigned long long*>(inter));
+    const uint64_t chunks = ((uint64_t)g->V + PART_CHUNK - 1) / PART_CHUNK;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned blocks = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(chunks, (uint64_t)sms * 8));
+    k_partition<<<blocks, 256, 0, st>>>(g->V, g->partitions, B, g->row_ptr, g->col, bounds,
+                                        reinterpret_cast<unsigned long long*>(inter));
     return cudaGetLastError();
 }
 

@@ -226,6 +226,21 @@ def test_solve_wait_limit_returns_timeout_and_device_stays_usable(sssp):
     check_solve(sssp, g, ref, [0])
 
 
+def test_autotune_picks_a_valid_schedule_and_caches_it(sssp, tmp_path, monkeypatch):
+    monkeypatch.setenv("SSSP_TUNE_CACHE", str(tmp_path / "tune.json"))
+    V = 30000
+    src, dst, w = raw_graph(77, V, 240000)
+    ref = oracle.csr(V, src, dst, w)
+    g = sssp.build_csr(V, src, dst, w, partitions=24)
+    srcs = np.array([1, 2, 29999], np.uint32)
+    opts, ms = sssp.autotune(g, srcs)
+    assert ms is not None and ms > 0 and opts.delta >= 1 and opts.tile in (1024, 2048, 4096)
+    assert opts.split in (1, 2, 4)
+    check_solve(sssp, g, ref, srcs.tolist(), opts)
+    again, ms2 = sssp.autotune(g, srcs)
+    assert ms2 is None and (again.delta, again.tile, again.split) == (opts.delta, opts.tile, opts.split)
+
+
 # ------------------------------------------------------------------------ K5
 
 def test_batched_parity_and_graph_replay(sssp):
