@@ -213,6 +213,9 @@ sssp_status sssp_autotune(const sssp_graph* g, const uint32_t* sources, uint32_t
     b.ev_relax_begin = b.ev_relax_end = nullptr;
     Resolved r;
     if (!resolve(&b, g->wtype, &r)) return SSSP_EINVAL;
+    b.threads = r.threads;  // report explicit values, not "default" zeros
+    b.tile = r.tile;
+    b.split = r.split;
     if (trials == 0) trials = 1;
     cudaStream_t st = (cudaStream_t)stream;
     // mean of a sample of the weights sets the scale of the bucket-width candidates
@@ -370,6 +373,7 @@ sssp_status prepare_batch(const sssp_batch* b, const sssp_options* opt, void* ws
     Resolved r;
     BatchTables t;
     if (!ws || !aligned16(ws) || !resolve(opt, b ? b->wtype : 0, &r) || !build_tables(b, &t)) return SSSP_EINVAL;
+    if (r.threads > SOLVE_MAX_THREADS) return SSSP_EINVAL;
     const BatchWs L = batch_layout(b->n_problems, t.total_out, t.total_words);
     if (ws_bytes < L.total) return SSSP_ENOMEM;
     char* base = static_cast<char*>(ws);

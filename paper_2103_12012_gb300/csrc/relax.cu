@@ -44,6 +44,7 @@ namespace {
 
 constexpr unsigned long long SRC_KEY = 0x00000000FFFFFFFFull;  // dist 0, pred NONE
 constexpr uint64_t KERNEL_LIMIT_FACTOR = 3;  // whole-kernel wall-clock limit = 3 x idle limit
+constexpr uint32_t MAX_SUBROUNDS = 256;       // local sub-rounds one round may run
 constexpr int EDGE_BATCH = 3;                // edges in flight per thread in phase E (measured: 2-4 similar)
 constexpr unsigned long long ROUND_RESERVE = 1ull << 32;  // termination counts reserved per round (> edges)
 
@@ -128,7 +129,7 @@ __device__ __forceinline__ uint32_t bucket_bound(uint32_t dmin, uint32_t delta) 
 }
 
 struct Scalars {
-    uint32_t cnt, nlist, dmin, nsel, nclaim, act, bad;
+    uint32_t cnt, nlist, dmin, nsel, nclaim, act, bad, nlq;
     int pick;
     unsigned long long prob;
 };
@@ -158,6 +159,7 @@ struct Smem {
     uint32_t* list_d;   // [tile]  A: queued distances; D/E: distance of taken vertex
     uint32_t* sel_v;    // [tile]  taken vertex ids
     uint32_t* sel_pref; // [tile+1] degree prefix sums
+    uint32_t* lq;       // [tile]  vertices of this unit lowered below the bucket bound (next sub-round)
     uint32_t* touched;  // [Qw] units that got a new queued vertex this round (static mode)
     uint32_t* wsum;     // [32]
     Scalars* sc;
@@ -263,94 +265,130 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
         myclaim = warp_sum(myclaim);
         if (lane == 0 && myclaim) atomicAdd(&sc.nclaim, myclaim);
         __syncthreads();
-        te = block_scan_excl(sm.sel_pref, nsel, sm.wsum);
-        if (tid == 0) sm.sel_pref[nsel] = te;
-        __syncthreads();
+        // Sub-rounds: a relaxation that lowers a vertex of this unit below the bucket
+        // bound queues it in shared memory (lq) and the next sub-round relaxes it, with
+        // no inbox bit and no rescan -- Dijkstra inside the partition (Alg. 3) until the
+        // bucket is exhausted or MAX_SUBROUNDS is reached.  Everything in lq is covered by
+        // this round's reservation; whatever is left in lq at the end gets inbox bits.
+        for (uint32_t sub = 0;; ++sub) {
+            te = block_scan_excl(sm.sel_pref, nsel, sm.wsum);
+            if (tid == 0) {
+                sm.sel_pref[nsel] = te;
+                sc.nlq = 0;
+                cnt.edges += te;
+            }
+            __syncthreads();
+            const bool last = sub + 1u >= MAX_SUBROUNDS;
 
-        // ---- E: relax all out-edges, edge-parallel.  Each thread keeps
-        // EDGE_BATCH independent edges in flight: all CSR loads, then all
-        // read-first filters, then all atomics, so their latencies overlap.
-        uint32_t lact = 0, bad = 0;
-        for (uint32_t k0 = tid; k0 < te; k0 += EDGE_BATCH * T) {
-            uint32_t vv[EDGE_BATCH], cc[EDGE_BATCH], aa[EDGE_BATCH];
-            uint32_t a = 0;
-#pragma unroll
-            for (int j = 0; j < EDGE_BATCH; ++j) {
-                const uint32_t k = k0 + (uint32_t)j * T;
-                vv[j] = NONE;
-                if (k < te) {
-                    uint32_t b = nsel;  // sel_pref[a] <= k < sel_pref[b]; a only grows with k
-                    while (b - a > 1u) {
-                        const uint32_t m = (a + b) >> 1;
-                        if (sm.sel_pref[m] <= k)
-                            a = m;
-                        else
-                            b = m;
-                    }
-                    const uint32_t e = sm.list_v[a] + (k - sm.sel_pref[a]);
-                    aa[j] = a;
-                    vv[j] = __ldg(&c.col[e]);
-                    cc[j] = __ldg(&c.w[e]);  // the weight, until it becomes the candidate below
-                }
-            }
-            unsigned long long cur[EDGE_BATCH];
-#pragma unroll
-            for (int j = 0; j < EDGE_BATCH; ++j) {
-                cur[j] = 0;
-                if (vv[j] == NONE) continue;
-                if (!W::weight_ok(cc[j]) || vv[j] >= c.V) {
-                    bad |= 1u;
-                    vv[j] = NONE;
-                    continue;
-                }
-                if (!W::add(sm.list_d[aa[j]], cc[j], cc[j])) {
-                    bad |= 2u;
-                    vv[j] = NONE;
-                    continue;
-                }
-                // read-first filter: a stale (higher) value only lets a useless atomic through
-                cur[j] = __ldcg(&c.packed[vv[j]]);
-            }
-            uint32_t improved = 0;
-#pragma unroll
-            for (int j = 0; j < EDGE_BATCH; ++j) {
-                if (vv[j] == NONE) continue;
-                const unsigned long long key = ((unsigned long long)cc[j] << 32) | sm.sel_v[aa[j]];
-                if (key < cur[j]) {
-                    ++cnt.atomics;
-                    const unsigned long long old = atomicMin(&c.packed[vv[j]], key);
-                    if (key < old && (uint32_t)(old >> 32) > cc[j]) improved |= 1u << j;
-                }
-            }
-            if (improved) {
-                // every lowered word before any of this thread's inbox bits (release)
-                __threadfence();
+            // ---- E: relax all out-edges, edge-parallel.  Each thread keeps
+            // EDGE_BATCH independent edges in flight: all CSR loads, then all
+            // read-first filters, then all atomics, so their latencies overlap.
+            uint32_t lact = 0, bad = 0;
+            for (uint32_t k0 = tid; k0 < te; k0 += EDGE_BATCH * T) {
+                uint32_t vv[EDGE_BATCH], cc[EDGE_BATCH], aa[EDGE_BATCH];
+                uint32_t a = 0;
 #pragma unroll
                 for (int j = 0; j < EDGE_BATCH; ++j) {
-                    if (!(improved & (1u << j))) continue;
-                    const uint32_t v = vv[j];
-                    ++cnt.improved;
-                    const uint32_t bit = 1u << (v & 31u);
-                    const uint32_t ob = atomicOr(&c.bitmap[v >> 5], bit);
-                    if (!(ob & bit)) {
-                        ++lact;
-                        if (STATIC) {
-                            const uint32_t p = v / c.B;
-                            const uint32_t q = p * c.split + (v - p * c.B) / c.Bq;
-                            if (q != my_q) ++cnt.remote;
-                            atomicOr(&sm.touched[q >> 5], 1u << (q & 31u));
+                    const uint32_t k = k0 + (uint32_t)j * T;
+                    vv[j] = NONE;
+                    if (k < te) {
+                        uint32_t b = nsel;  // sel_pref[a] <= k < sel_pref[b]; a only grows with k
+                        while (b - a > 1u) {
+                            const uint32_t m = (a + b) >> 1;
+                            if (sm.sel_pref[m] <= k)
+                                a = m;
+                            else
+                                b = m;
+                        }
+                        const uint32_t e = sm.list_v[a] + (k - sm.sel_pref[a]);
+                        aa[j] = a;
+                        vv[j] = __ldg(&c.col[e]);
+                        cc[j] = __ldg(&c.w[e]);  // the weight, until it becomes the candidate below
+                    }
+                }
+                unsigned long long cur[EDGE_BATCH];
+#pragma unroll
+                for (int j = 0; j < EDGE_BATCH; ++j) {
+                    cur[j] = 0;
+                    if (vv[j] == NONE) continue;
+                    if (!W::weight_ok(cc[j]) || vv[j] >= c.V) {
+                        bad |= 1u;
+                        vv[j] = NONE;
+                        continue;
+                    }
+                    if (!W::add(sm.list_d[aa[j]], cc[j], cc[j])) {
+                        bad |= 2u;
+                        vv[j] = NONE;
+                        continue;
+                    }
+                    // read-first filter: a stale (higher) value only lets a useless atomic through
+                    cur[j] = __ldcg(&c.packed[vv[j]]);
+                }
+                uint32_t improved = 0;
+#pragma unroll
+                for (int j = 0; j < EDGE_BATCH; ++j) {
+                    if (vv[j] == NONE) continue;
+                    const unsigned long long key = ((unsigned long long)cc[j] << 32) | sm.sel_v[aa[j]];
+                    if (key < cur[j]) {
+                        ++cnt.atomics;
+                        const unsigned long long old = atomicMin(&c.packed[vv[j]], key);
+                        if (key < old && (uint32_t)(old >> 32) > cc[j]) {
+                            ++cnt.improved;
+                            // near and in this unit: relax it in the next sub-round
+                            if (!last && vv[j] >= lo && vv[j] < hi && cc[j] < thr) {
+                                const uint32_t pos = atomicAdd(&sc.nlq, 1u);
+                                if (pos < c.tile) {
+                                    sm.lq[pos] = vv[j];
+                                    continue;
+                                }
+                            }
+                            improved |= 1u << j;
+                        }
+                    }
+                }
+                if (improved) {
+                    // every lowered word before any of this thread's inbox bits (release)
+                    __threadfence();
+#pragma unroll
+                    for (int j = 0; j < EDGE_BATCH; ++j) {
+                        if (!(improved & (1u << j))) continue;
+                        const uint32_t v = vv[j];
+                        const uint32_t bit = 1u << (v & 31u);
+                        const uint32_t ob = atomicOr(&c.bitmap[v >> 5], bit);
+                        if (!(ob & bit)) {
+                            ++lact;
+                            if (STATIC) {
+                                const uint32_t p = v / c.B;
+                                const uint32_t q = p * c.split + (v - p * c.B) / c.Bq;
+                                if (q != my_q) ++cnt.remote;
+                                atomicOr(&sm.touched[q >> 5], 1u << (q & 31u));
+                            }
                         }
                     }
                 }
             }
+            lact = warp_sum(lact);
+            bad = __reduce_or_sync(0xFFFFFFFFu, bad);
+            if (lane == 0) {
+                if (lact) atomicAdd(&sc.act, lact);
+                if (bad) atomicOr(&sc.bad, bad);
+            }
+            __syncthreads();
+            const uint32_t nlq = min(sc.nlq, c.tile);
+            if (nlq == 0) break;
+            // the next sub-round's entries: the queued local vertices with fresh distances
+            for (uint32_t i = tid; i < nlq; i += T) {
+                const uint32_t u = sm.lq[i];
+                sm.sel_v[i] = u;
+                sm.list_d[i] = (uint32_t)(__ldcg(&c.packed[u]) >> 32);
+                const uint32_t beg = __ldg(&c.row_ptr[u]);
+                sm.list_v[i] = beg;
+                sm.sel_pref[i] = __ldg(&c.row_ptr[u + 1]) - beg;
+            }
+            if (tid == 0) cnt.verts += nlq;
+            nsel = nlq;
+            __syncthreads();
         }
-        lact = warp_sum(lact);
-        bad = __reduce_or_sync(0xFFFFFFFFu, bad);
-        if (lane == 0) {
-            if (lact) atomicAdd(&sc.act, lact);
-            if (bad) atomicOr(&sc.bad, bad);
-        }
-        __syncthreads();
     }
 
     // ---- F: settle the count, ring doorbells (warp 0)
@@ -375,7 +413,6 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
             if (tid == 0 && found > sc.nclaim) st_relaxed(&c.dirty[my_q], 1u);  // more left in this unit
         }
         if (tid == 0 && found) {
-            cnt.edges += te;
             cnt.rounds += 1;
             cnt.verts += sc.nclaim;
             cnt.acts += sc.act;
@@ -393,7 +430,8 @@ __device__ Smem carve(uint32_t* dsm, uint32_t tile, uint32_t Qw, uint32_t* wsum,
     s.list_d = dsm + tile;
     s.sel_v = dsm + 2 * tile;
     s.sel_pref = dsm + 3 * tile;
-    s.touched = dsm + 4 * tile + 1;
+    s.lq = dsm + 4 * tile + 1;
+    s.touched = s.lq + tile;
     s.wsum = wsum;
     s.sc = sc;
     (void)Qw;
@@ -553,9 +591,10 @@ __global__ void __launch_bounds__(SOLVE_MAX_THREADS, 4) k_solve(SolveLaunch L) {
     flush_counters(L.hdr, cnt);
 }
 
-// K5: persistent, dynamic: blocks pull whole problems from a work queue.
+// K5: persistent, dynamic: blocks pull whole problems from a work queue (four
+// 512-thread blocks per SM, as for K4).
 template <class W>
-__global__ void __launch_bounds__(1024) k_batched(BatchLaunch L) {
+__global__ void __launch_bounds__(SOLVE_MAX_THREADS, 4) k_batched(BatchLaunch L) {
     extern __shared__ uint32_t dsm[];
     __shared__ uint32_t wsum[32];
     __shared__ Scalars sc;
@@ -635,7 +674,7 @@ cudaError_t set_smem(K kernel, size_t smem) {
 }  // namespace
 
 size_t relax_smem_bytes(uint32_t tile, uint32_t Q) {
-    return (size_t)(4u * tile + 1u) * 4u + (size_t)((Q + 31u) / 32u) * 4u;
+    return (size_t)(5u * tile + 1u) * 4u + (size_t)((Q + 31u) / 32u) * 4u;
 }
 
 cudaError_t relax_max_blocks_per_sm(int wtype, uint32_t threads, uint32_t tile, uint32_t Q, int* out) {
