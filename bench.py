@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--split", type=int, default=0)
     ap.add_argument("--no-tune", action="store_true", help="library defaults instead of the autotuned schedule")
+    ap.add_argument("--profile-case", choices=["batched", "backward", "prune"],
+                    help="run a small case of one kernel three times and exit (for ncu captures)")
     return ap.parse_args()
 
 
@@ -489,9 +491,44 @@ def extras(sssp, dev):
     return out
 
 
+def profile_case(which):
+    """Small cases of the other kernels for ncu: batched (64 graphs x 16 sources), backward (R-MAT scale 18
+    fp32, 32 sources), Trishla prune (R-MAT scale 16, local mode)."""
+    import torch
+
+    import paper_2103_12012_gb300 as sssp
+    if which == "batched":
+        graphs0, sources = gg.workload_batch512(n_graphs=64)
+        graphs = [sssp.build_csr(g.V, g.src, g.dst, g.w) for g in graphs0]
+        b = sssp.Batch(graphs, sources)
+        for _ in range(3):
+            b.solve()
+        st, stats = b.status()
+        assert st == sssp.SSSP_OK, st
+        print("batched", b.n_problems, stats)
+    elif which == "backward":
+        g0, srcs, gup = gg.workload_rmat18_f32()
+        g = sssp.build_csr(g0.V, g0.src, g0.dst, g0.w, partitions=8)
+        _, pred, st, _ = sssp.solve(g, srcs)
+        gd = torch.from_numpy(gup).cuda()
+        for _ in range(3):
+            gr = sssp.backward(g, pred, gd)
+        torch.cuda.synchronize()
+        print("backward", float(gr.abs().sum()))
+    else:
+        g0 = gg.rmat(gg.BASE_SEED + 16, 16, 16 << 16)
+        g = sssp.build_csr(g0.V, g0.src, g0.dst, g0.w, partitions=16)
+        for _ in range(3):
+            keep, _ = sssp.prune(g, 0)
+        torch.cuda.synchronize()
+        print("prune", int((keep == 0).sum()), "of", g.E)
+
+
 if __name__ == "__main__":
     args = parse()
-    if args.impl == "reference":
+    if args.profile_case:
+        profile_case(args.profile_case)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
