@@ -402,6 +402,43 @@ class Batch:
         _check(lib().sssp_solve_batched(ctypes.byref(self.c), ctypes.byref(self.opts), _ptr(self.ws), self.ws_bytes,
                                         _stream(stream)), "sssp_solve_batched")
 
+    def autotune(self, deltas=(2, 4, 8, 16, 32, 64), tiles=(256, 512, 1024, 2048), stream=None):
+        """Choose the batched kernel's bucket width and tile by timing sssp_solve_batched on this batch
+        (coordinate search: delta, then tile).  Sets self.opts and returns (options, ms)."""
+        torch = _torch()
+
+        def run(o):
+            self.opts = o
+            self.solve(stream)
+            st, _ = self.status(stream)
+            if st != SSSP_OK:
+                return float("inf")
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            self.solve(stream)
+            b.record()
+            st, _ = self.status(stream)
+            return a.elapsed_time(b) if st == SSSP_OK else float("inf")
+
+        base = self.opts
+        best, best_ms = base, run(base)
+        for d in deltas:
+            o = options(threads=base.threads, tile=base.tile, delta=d)
+            ms = run(o)
+            if ms < best_ms:
+                best, best_ms = o, ms
+        for t in tiles:
+            o = options(threads=best.threads, tile=t, delta=best.delta)
+            ms = run(o)
+            if ms < best_ms:
+                best, best_ms = o, ms
+        self.opts = best
+        if self.plan is not None:
+            lib().sssp_batch_plan_destroy(self.plan)
+            self.plan = None
+        return best, best_ms
+
     def make_plan(self, stream=None):
         h = ctypes.c_void_p()
         _check(lib().sssp_batch_plan_create(ctypes.byref(self.c), ctypes.byref(self.opts), _ptr(self.ws),
