@@ -280,26 +280,27 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
             __syncthreads();
             const bool last = sub + 1u >= MAX_SUBROUNDS;
 
-            // ---- E: relax all out-edges, edge-parallel.  Each thread keeps
-            // EDGE_BATCH independent edges in flight: all CSR loads, then all
-            // read-first filters, then all atomics, so their latencies overlap.
+            // ---- E: relax all out-edges, edge-parallel.  Each thread takes
+            // EDGE_BATCH consecutive edges (one search of the degree prefix, then
+            // steps over row ends) and keeps them in flight together: all CSR
+            // loads, then all read-first filters, then all atomics.
             uint32_t lact = 0, bad = 0;
-            for (uint32_t k0 = tid; k0 < te; k0 += EDGE_BATCH * T) {
+            for (uint32_t k0 = tid * EDGE_BATCH; k0 < te; k0 += EDGE_BATCH * T) {
                 uint32_t vv[EDGE_BATCH], cc[EDGE_BATCH], aa[EDGE_BATCH];
-                uint32_t a = 0;
+                uint32_t a = 0, b = nsel;  // sel_pref[a] <= k0 < sel_pref[b]
+                while (b - a > 1u) {
+                    const uint32_t m = (a + b) >> 1;
+                    if (sm.sel_pref[m] <= k0)
+                        a = m;
+                    else
+                        b = m;
+                }
 #pragma unroll
                 for (int j = 0; j < EDGE_BATCH; ++j) {
-                    const uint32_t k = k0 + (uint32_t)j * T;
+                    const uint32_t k = k0 + (uint32_t)j;
                     vv[j] = NONE;
                     if (k < te) {
-                        uint32_t b = nsel;  // sel_pref[a] <= k < sel_pref[b]; a only grows with k
-                        while (b - a > 1u) {
-                            const uint32_t m = (a + b) >> 1;
-                            if (sm.sel_pref[m] <= k)
-                                a = m;
-                            else
-                                b = m;
-                        }
+                        while (sm.sel_pref[a + 1u] <= k) ++a;  // sel_pref[nsel] = te > k ends it
                         const uint32_t e = sm.list_v[a] + (k - sm.sel_pref[a]);
                         aa[j] = a;
                         vv[j] = __ldg(&c.col[e]);
