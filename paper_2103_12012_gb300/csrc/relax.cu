@@ -45,6 +45,8 @@ namespace {
 constexpr unsigned long long SRC_KEY = 0x00000000FFFFFFFFull;  // dist 0, pred NONE
 constexpr uint64_t KERNEL_LIMIT_FACTOR = 3;  // whole-kernel wall-clock limit = 3 x idle limit
 constexpr uint32_t MAX_SUBROUNDS = 256;       // local sub-rounds one round may run
+constexpr uint32_t GATHER_MIN = 1024;          // queued vertices one scan can keep (at least)
+constexpr int GATHER_G = 2;                   // queued vertices a lane enumerates and loads together
 constexpr int EDGE_BATCH = 3;                // edges in flight per thread in phase E (measured: 2-4 similar)
 constexpr unsigned long long ROUND_RESERVE = 1ull << 32;  // termination counts reserved per round (> edges)
 
@@ -86,6 +88,44 @@ __device__ __forceinline__ uint32_t range_mask(uint32_t wd, uint32_t lo, uint32_
 
 // In-place exclusive scan of a[0..n) in shared memory by the whole block;
 // returns the total.  wsum: 32 words of shared scratch.
+__device__ __forceinline__ uint32_t warp_scan_incl(uint32_t x, uint32_t lane) {
+#pragma unroll
+    for (uint32_t o = 1; o < 32u; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
+// The vertex of the i-th set bit (i < the warp's total) of the 32 inbox words
+// wb .. wb+31 a warp holds, one per lane: `bits` the lane's word, `incl` the
+// inclusive prefix of the popcounts.  Binary lifting finds the word over the
+// lanes' prefixes, then the bit over the word's prefix popcounts.
+__device__ __forceinline__ uint32_t nth_queued(uint32_t wb, uint32_t bits, uint32_t incl, uint32_t i) {
+    uint32_t w = 0;
+#pragma unroll
+    for (uint32_t s = 16; s; s >>= 1)
+        if (__shfl_sync(0xFFFFFFFFu, incl, w + s - 1u) <= i) w += s;
+    const uint32_t wbits = __shfl_sync(0xFFFFFFFFu, bits, w);
+    const uint32_t r = i - (__shfl_sync(0xFFFFFFFFu, incl, w) - __popc(wbits));
+    uint32_t p = 0;  // largest p with fewer than r+1 set bits below it
+#pragma unroll
+    for (uint32_t s = 16; s; s >>= 1)
+        if ((uint32_t)__popc(wbits & ((1u << (p + s)) - 1u)) <= r) p += s;
+    return (wb + w) * 32u + p;
+}
+
+// Appends v to list[0, cap) for the lanes with `take` (one shared atomic per warp).
+__device__ __forceinline__ void warp_append(bool take, uint32_t v, uint32_t* list, uint32_t* count, uint32_t cap,
+                                            uint32_t lane) {
+    const uint32_t ball = __ballot_sync(0xFFFFFFFFu, take);
+    if (!ball) return;
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(count, (uint32_t)__popc(ball));
+    base = __shfl_sync(0xFFFFFFFFu, base, 0) + (uint32_t)__popc(ball & ((1u << lane) - 1u));
+    if (take && base < cap) list[base] = v;
+}
+
 __device__ uint32_t block_scan_excl(uint32_t* a, uint32_t n, uint32_t* wsum) {
     const uint32_t T = blockDim.x, tid = threadIdx.x, lane = tid & 31u, wid = tid >> 5, nw = T >> 5;
     const uint32_t chunk = (n + T - 1u) / T;
@@ -134,10 +174,9 @@ struct Scalars {
     unsigned long long prob;
 };
 
-struct Counters {
-    unsigned long long edges, acts, rounds, verts, idle_ns;  // kept by thread 0
-    uint32_t atomics, improved, remote;             // kept per thread (statistics only)
-};
+// Block statistics in shared memory, in sssp_stats order (idle time in ns until
+// the flush): kept there rather than in registers every thread would carry.
+enum : int { ST_EDGES, ST_ATOMICS, ST_IMPROVED, ST_ACTS, ST_ROUNDS, ST_VERTS, ST_REMOTE, ST_IDLE, ST_N };
 
 // Per-round view of one problem (one source on one graph).
 struct Ctx {
@@ -148,28 +187,29 @@ struct Ctx {
     unsigned long long* packed;
     uint32_t* bitmap;
     WsHeader* hdr;
-    uint32_t delta, tile;
+    uint32_t delta, tile, gcap;
     // static-ownership mode only
     uint32_t* dirty;  // this source's unit doorbells
     uint32_t B, Bq, split, Qw;
 };
 
 struct Smem {
-    uint32_t* list_v;   // [tile]  A: queued ids;       D/E: row start of taken vertex
-    uint32_t* list_d;   // [tile]  A: queued distances; D/E: distance of taken vertex
+    uint32_t* list_v;   // [gcap]  A: queued ids;       D/E: row start of taken vertex
+    uint32_t* list_d;   // [gcap]  A: queued distances; D/E: distance of taken vertex
     uint32_t* sel_v;    // [tile]  taken vertex ids
     uint32_t* sel_pref; // [tile+1] degree prefix sums
     uint32_t* lq;       // [tile]  vertices of this unit lowered below the bucket bound (next sub-round)
     uint32_t* touched;  // [Qw] units that got a new queued vertex this round (static mode)
     uint32_t* wsum;     // [32]
     Scalars* sc;
+    unsigned long long* st;  // [ST_N] block statistics
 };
 
 // One round over the unit owning vertices [lo, hi).  Returns the number of
 // queued vertices the scan found (0 = the unit's inbox was empty).
 template <class W, bool STATIC>
-__device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t my_q, const Smem& sm,
-                                Counters& cnt) {
+__device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t my_q,
+                                const Smem& sm) {
     const uint32_t T = blockDim.x, tid = threadIdx.x, lane = tid & 31u;
     Scalars& sc = *sm.sc;
     if (tid == 0) {
@@ -190,22 +230,41 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
     }
     __syncthreads();
 
-    // ---- A: scan the inbox, gather queued vertices and their distances
+    // ---- A: scan the inbox, gather queued vertices and their distances.  Each
+    // warp takes 32 words; its lanes then enumerate the set bits by rank, GATHER_G
+    // each with their distance loads in flight together.
     const uint32_t wlo = lo >> 5, whi = (hi - 1u) >> 5;
     uint32_t lmin = 0xFFFFFFFFu, lcnt = 0;
-    for (uint32_t wd = wlo + tid; wd <= whi; wd += T) {
-        uint32_t bits = ld_relaxed(&c.bitmap[wd]) & range_mask(wd, lo, hi);
-        while (bits) {
-            const uint32_t b = __ffs(bits) - 1u;
-            bits &= bits - 1u;
-            const uint32_t v = wd * 32u + b;
-            const uint32_t d = (uint32_t)(__ldcg(&c.packed[v]) >> 32);
-            lmin = min(lmin, d);
-            ++lcnt;
-            const uint32_t idx = atomicAdd(&sc.nlist, 1u);
-            if (idx < c.tile) {
-                sm.list_v[idx] = v;
-                sm.list_d[idx] = d;
+    for (uint32_t wb = wlo + (tid & ~31u); wb <= whi; wb += T) {
+        const uint32_t wd = wb + lane;
+        const uint32_t bits = wd <= whi ? ld_relaxed(&c.bitmap[wd]) & range_mask(wd, lo, hi) : 0u;
+        const uint32_t incl = warp_scan_incl((uint32_t)__popc(bits), lane);
+        const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        if (total == 0) continue;
+        uint32_t base = 0;
+        if (lane == 0) {
+            base = atomicAdd(&sc.nlist, total);
+            lcnt += total;
+        }
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        for (uint32_t i0 = lane; i0 < total + lane; i0 += 32u * GATHER_G) {  // warp-uniform trip count
+            uint32_t vs[GATHER_G], ds[GATHER_G];
+#pragma unroll
+            for (int g = 0; g < GATHER_G; ++g)
+                vs[g] = nth_queued(wb, bits, incl, min(i0 + 32u * g, total - 1u));
+#pragma unroll
+            for (int g = 0; g < GATHER_G; ++g)
+                if (i0 + 32u * g < total) ds[g] = (uint32_t)(__ldcg(&c.packed[vs[g]]) >> 32);
+#pragma unroll
+            for (int g = 0; g < GATHER_G; ++g) {
+                const uint32_t i = i0 + 32u * g;
+                if (i < total) {
+                    lmin = min(lmin, ds[g]);
+                    if (base + i < c.gcap) {
+                        sm.list_v[base + i] = vs[g];
+                        sm.list_d[base + i] = ds[g];
+                    }
+                }
             }
         }
     }
@@ -221,21 +280,30 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
     if (found != 0) {
         const uint32_t thr = bucket_bound<W>(sc.dmin, c.delta);
 
-        // ---- B: the near bucket, at most `tile` vertices
-        if (found <= c.tile) {
-            for (uint32_t i = tid; i < found; i += T)
-                if (sm.list_d[i] < thr) sm.sel_v[atomicAdd(&sc.nsel, 1u)] = sm.list_v[i];
+        // ---- B: the near bucket, at most `tile` vertices: from the gathered list,
+        // or, when the scan found more than it keeps, by enumerating the inbox again
+        if (found <= c.gcap) {
+            for (uint32_t i = tid; i < found + lane; i += T) {  // warp-uniform trip count
+                const bool take = i < found && sm.list_d[i] < thr;
+                warp_append(take, take ? sm.list_v[i] : 0u, sm.sel_v, &sc.nsel, c.tile, lane);
+            }
         } else {
-            for (uint32_t wd = wlo + tid; wd <= whi; wd += T) {
-                uint32_t bits = ld_relaxed(&c.bitmap[wd]) & range_mask(wd, lo, hi);
-                while (bits) {
-                    const uint32_t b = __ffs(bits) - 1u;
-                    bits &= bits - 1u;
-                    const uint32_t v = wd * 32u + b;
-                    if ((uint32_t)(__ldcg(&c.packed[v]) >> 32) < thr) {
-                        const uint32_t j = atomicAdd(&sc.nsel, 1u);
-                        if (j < c.tile) sm.sel_v[j] = v;
-                    }
+            for (uint32_t wb = wlo + (tid & ~31u); wb <= whi; wb += T) {
+                const uint32_t wd = wb + lane;
+                const uint32_t bits = wd <= whi ? ld_relaxed(&c.bitmap[wd]) & range_mask(wd, lo, hi) : 0u;
+                const uint32_t incl = warp_scan_incl((uint32_t)__popc(bits), lane);
+                const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+                for (uint32_t i0 = lane; i0 < total + lane; i0 += 32u * GATHER_G) {
+                    uint32_t vs[GATHER_G], ds[GATHER_G];
+#pragma unroll
+                    for (int g = 0; g < GATHER_G; ++g)
+                        vs[g] = nth_queued(wb, bits, incl, min(i0 + 32u * g, total - 1u));
+#pragma unroll
+                    for (int g = 0; g < GATHER_G; ++g)
+                        ds[g] = i0 + 32u * g < total ? (uint32_t)(__ldcg(&c.packed[vs[g]]) >> 32) : 0xFFFFFFFFu;
+#pragma unroll
+                    for (int g = 0; g < GATHER_G; ++g)
+                        warp_append(ds[g] < thr, vs[g], sm.sel_v, &sc.nsel, c.tile, lane);
                 }
             }
         }
@@ -275,7 +343,7 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
             if (tid == 0) {
                 sm.sel_pref[nsel] = te;
                 sc.nlq = 0;
-                cnt.edges += te;
+                sm.st[ST_EDGES] += te;
             }
             __syncthreads();
             const bool last = sub + 1u >= MAX_SUBROUNDS;
@@ -285,6 +353,7 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
             // steps over row ends) and keeps them in flight together: all CSR
             // loads, then all read-first filters, then all atomics.
             uint32_t lact = 0, bad = 0;
+            uint32_t n_ai = 0, n_rem = 0;  // statistics: atomics | improved << 16, remote activations
             for (uint32_t k0 = tid * EDGE_BATCH; k0 < te; k0 += EDGE_BATCH * T) {
                 uint32_t vv[EDGE_BATCH], cc[EDGE_BATCH], aa[EDGE_BATCH];
                 uint32_t a = 0, b = nsel;  // sel_pref[a] <= k0 < sel_pref[b]
@@ -331,10 +400,10 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
                     if (vv[j] == NONE) continue;
                     const unsigned long long key = ((unsigned long long)cc[j] << 32) | sm.sel_v[aa[j]];
                     if (key < cur[j]) {
-                        ++cnt.atomics;
+                        n_ai += 1u;
                         const unsigned long long old = atomicMin(&c.packed[vv[j]], key);
                         if (key < old && (uint32_t)(old >> 32) > cc[j]) {
-                            ++cnt.improved;
+                            n_ai += 1u << 16;
                             // near and in this unit: relax it in the next sub-round
                             if (!last && vv[j] >= lo && vv[j] < hi && cc[j] < thr) {
                                 const uint32_t pos = atomicAdd(&sc.nlq, 1u);
@@ -346,6 +415,11 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
                             improved |= 1u << j;
                         }
                     }
+                }
+                if (n_ai & 0x80008000u) {  // keep both 16-bit halves from overflowing
+                    atomicAdd(&sm.st[ST_ATOMICS], (unsigned long long)(n_ai & 0xFFFFu));
+                    atomicAdd(&sm.st[ST_IMPROVED], (unsigned long long)(n_ai >> 16));
+                    n_ai = 0;
                 }
                 if (improved) {
                     // every lowered word before any of this thread's inbox bits (release)
@@ -361,7 +435,7 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
                             if (STATIC) {
                                 const uint32_t p = v / c.B;
                                 const uint32_t q = p * c.split + (v - p * c.B) / c.Bq;
-                                if (q != my_q) ++cnt.remote;
+                                if (q != my_q) ++n_rem;
                                 atomicOr(&sm.touched[q >> 5], 1u << (q & 31u));
                             }
                         }
@@ -370,6 +444,14 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
             }
             lact = warp_sum(lact);
             bad = __reduce_or_sync(0xFFFFFFFFu, bad);
+            {
+                const uint32_t wa = warp_sum(n_ai & 0xFFFFu), wi = warp_sum(n_ai >> 16), wr = warp_sum(n_rem);
+                if (lane == 0) {
+                    if (wa) atomicAdd(&sm.st[ST_ATOMICS], (unsigned long long)wa);
+                    if (wi) atomicAdd(&sm.st[ST_IMPROVED], (unsigned long long)wi);
+                    if (wr) atomicAdd(&sm.st[ST_REMOTE], (unsigned long long)wr);
+                }
+            }
             if (lane == 0) {
                 if (lact) atomicAdd(&sc.act, lact);
                 if (bad) atomicOr(&sc.bad, bad);
@@ -386,7 +468,7 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
                 sm.list_v[i] = beg;
                 sm.sel_pref[i] = __ldg(&c.row_ptr[u + 1]) - beg;
             }
-            if (tid == 0) cnt.verts += nlq;
+            if (tid == 0) sm.st[ST_VERTS] += nlq;
             nsel = nlq;
             __syncthreads();
         }
@@ -414,9 +496,9 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
             if (tid == 0 && found > sc.nclaim) st_relaxed(&c.dirty[my_q], 1u);  // more left in this unit
         }
         if (tid == 0 && found) {
-            cnt.rounds += 1;
-            cnt.verts += sc.nclaim;
-            cnt.acts += sc.act;
+            sm.st[ST_ROUNDS] += 1;
+            sm.st[ST_VERTS] += sc.nclaim;
+            sm.st[ST_ACTS] += sc.act;
             if (sc.bad & 1u) set_status(c.hdr, SSSP_EINVAL);
             if (sc.bad & 2u) set_status(c.hdr, SSSP_EOVERFLOW);
         }
@@ -425,29 +507,31 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
     return found;
 }
 
-__device__ Smem carve(uint32_t* dsm, uint32_t tile, uint32_t Qw, uint32_t* wsum, Scalars* sc) {
+__host__ __device__ inline uint32_t gather_cap(uint32_t tile) { return tile > GATHER_MIN ? tile : GATHER_MIN; }
+
+__device__ Smem carve(uint32_t* dsm, uint32_t tile, uint32_t Qw, uint32_t* wsum, Scalars* sc,
+                      unsigned long long* st) {
+    const uint32_t gcap = gather_cap(tile);
     Smem s;
     s.list_v = dsm;
-    s.list_d = dsm + tile;
-    s.sel_v = dsm + 2 * tile;
-    s.sel_pref = dsm + 3 * tile;
-    s.lq = dsm + 4 * tile + 1;
+    s.list_d = dsm + gcap;
+    s.sel_v = dsm + 2 * gcap;
+    s.sel_pref = s.sel_v + tile;
+    s.lq = s.sel_pref + tile + 1;
     s.touched = s.lq + tile;
     s.wsum = wsum;
     s.sc = sc;
+    s.st = st;
+    for (uint32_t i = threadIdx.x; i < ST_N; i += blockDim.x) st[i] = 0ull;
     (void)Qw;
     return s;
 }
 
-__device__ void flush_counters(WsHeader* h, const Counters& c) {
-    // counters accumulated per thread (atomics/improved/remote) or by thread 0 (the rest)
-    // stats order follows sssp_stats
-    const unsigned long long v[8] = {c.edges, c.atomics, c.improved, c.acts, c.rounds, c.verts, c.remote,
-                                     c.idle_ns / 1000ull};
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const unsigned long long x = warp_sum64(v[i]);
-        if ((threadIdx.x & 31u) == 0 && x) atomicAdd(&h->stats[i], x);
+__device__ void flush_stats(WsHeader* h, const unsigned long long* st) {
+    const uint32_t i = threadIdx.x;
+    if (i < ST_N) {
+        const unsigned long long x = i == ST_IDLE ? st[i] / 1000ull : st[i];
+        if (x) atomicAdd(&h->stats[i], x);
     }
 }
 
@@ -503,8 +587,9 @@ __global__ void __launch_bounds__(SOLVE_MAX_THREADS, 4) k_solve(SolveLaunch L) {
     extern __shared__ uint32_t dsm[];
     __shared__ uint32_t wsum[32];
     __shared__ Scalars sc;
+    __shared__ unsigned long long st[ST_N];
     const uint32_t Qw = (L.Q + 31u) / 32u;
-    const Smem sm = carve(dsm, L.tile, Qw, wsum, &sc);
+    const Smem sm = carve(dsm, L.tile, Qw, wsum, &sc, st);
     for (uint32_t i = threadIdx.x; i < Qw; i += blockDim.x) sm.touched[i] = 0u;
     __syncthreads();
 
@@ -513,7 +598,6 @@ __global__ void __launch_bounds__(SOLVE_MAX_THREADS, 4) k_solve(SolveLaunch L) {
     uint32_t rr = 0, backoff = 32;
     uint64_t idle_start = 0;
     const uint64_t t_begin = globaltimer_ns();
-    Counters cnt = {};
     Ctx c;
     c.row_ptr = L.row_ptr;
     c.col = L.col;
@@ -522,6 +606,7 @@ __global__ void __launch_bounds__(SOLVE_MAX_THREADS, 4) k_solve(SolveLaunch L) {
     c.hdr = L.hdr;
     c.delta = L.delta_bits;
     c.tile = L.tile;
+    c.gcap = gather_cap(L.tile);
     c.B = L.B;
     c.Bq = L.Bq;
     c.split = L.split;
@@ -549,12 +634,12 @@ __global__ void __launch_bounds__(SOLVE_MAX_THREADS, 4) k_solve(SolveLaunch L) {
                 }
                 if (pick >= 0) {
                     __threadfence();  // doorbell before the inbox scan
-                    if (idle_start) cnt.idle_ns += globaltimer_ns() - idle_start;
+                    if (idle_start) sm.st[ST_IDLE] += globaltimer_ns() - idle_start;
                     idle_start = 0;
                     backoff = 32;
                 } else if (ld_relaxed(&L.hdr->pending) == 0ull) {
                     pick = -2;  // nothing queued, nothing in flight: terminated
-                    if (idle_start) cnt.idle_ns += globaltimer_ns() - idle_start;
+                    if (idle_start) sm.st[ST_IDLE] += globaltimer_ns() - idle_start;
                 } else {
                     const uint64_t now = globaltimer_ns();
                     if (idle_start == 0) {
@@ -587,9 +672,10 @@ __global__ void __launch_bounds__(SOLVE_MAX_THREADS, 4) k_solve(SolveLaunch L) {
         c.packed = L.packed + (size_t)s * L.V;
         c.bitmap = L.bitmap + (size_t)s * L.words;
         c.dirty = L.dirty + (size_t)s * L.Q;
-        relax_round<W, true>(c, lo, hi, q, sm, cnt);
+        relax_round<W, true>(c, lo, hi, q, sm);
     }
-    flush_counters(L.hdr, cnt);
+    __syncthreads();
+    flush_stats(L.hdr, sm.st);
 }
 
 // K5: persistent, dynamic: blocks pull whole problems from a work queue (four
@@ -599,12 +685,13 @@ __global__ void __launch_bounds__(SOLVE_MAX_THREADS, 4) k_batched(BatchLaunch L)
     extern __shared__ uint32_t dsm[];
     __shared__ uint32_t wsum[32];
     __shared__ Scalars sc;
-    const Smem sm = carve(dsm, L.tile, 0u, wsum, &sc);
-    Counters cnt = {};
+    __shared__ unsigned long long st[ST_N];
+    const Smem sm = carve(dsm, L.tile, 0u, wsum, &sc, st);
     Ctx c;
     c.hdr = L.hdr;
     c.delta = L.delta_bits;
     c.tile = L.tile;
+    c.gcap = gather_cap(L.tile);
     c.dirty = nullptr;
     c.B = c.Bq = c.split = 1u;
     c.Qw = 0;
@@ -640,7 +727,7 @@ __global__ void __launch_bounds__(SOLVE_MAX_THREADS, 4) k_batched(BatchLaunch L)
         }
         __syncthreads();
         for (;;) {
-            const uint32_t found = relax_round<W, false>(c, 0u, P.V, 0u, sm, cnt);
+            const uint32_t found = relax_round<W, false>(c, 0u, P.V, 0u, sm);
             if (tid == 0) {
                 int go = found != 0u;
                 if (go && globaltimer_ns() - t_begin > KERNEL_LIMIT_FACTOR * L.timeout_ns) {
@@ -664,7 +751,8 @@ __global__ void __launch_bounds__(SOLVE_MAX_THREADS, 4) k_batched(BatchLaunch L)
         }
         __syncthreads();
     }
-    flush_counters(L.hdr, cnt);
+    __syncthreads();
+    flush_stats(L.hdr, sm.st);
 }
 
 template <class K>
@@ -675,7 +763,7 @@ cudaError_t set_smem(K kernel, size_t smem) {
 }  // namespace
 
 size_t relax_smem_bytes(uint32_t tile, uint32_t Q) {
-    return (size_t)(5u * tile + 1u) * 4u + (size_t)((Q + 31u) / 32u) * 4u;
+    return (size_t)(2u * gather_cap(tile) + 3u * tile + 1u) * 4u + (size_t)((Q + 31u) / 32u) * 4u;
 }
 
 cudaError_t relax_max_blocks_per_sm(int wtype, uint32_t threads, uint32_t tile, uint32_t Q, int* out) {
