@@ -172,6 +172,9 @@ struct Scalars {
     uint32_t cnt, nlist, dmin, nsel, nclaim, act, bad, nlq;
     int pick;
     unsigned long long prob;
+    // thread 0's scheduling state (static mode), here rather than in every thread's registers
+    uint32_t rr, backoff;
+    unsigned long long idle_start, t_begin;
 };
 
 // Block statistics in shared memory, in sssp_stats order (idle time in ns until
@@ -593,11 +596,12 @@ __global__ void __launch_bounds__(SOLVE_MAX_THREADS, 4) k_solve(SolveLaunch L) {
     for (uint32_t i = threadIdx.x; i < Qw; i += blockDim.x) sm.touched[i] = 0u;
     __syncthreads();
 
-    const uint32_t U = L.S * L.Q;
-    const uint32_t nu = blockIdx.x < U ? (U - 1u - blockIdx.x) / gridDim.x + 1u : 0u;
-    uint32_t rr = 0, backoff = 32;
-    uint64_t idle_start = 0;
-    const uint64_t t_begin = globaltimer_ns();
+    if (threadIdx.x == 0) {
+        sc.rr = 0;
+        sc.backoff = 32;
+        sc.idle_start = 0;
+        sc.t_begin = globaltimer_ns();
+    }
     Ctx c;
     c.row_ptr = L.row_ptr;
     c.col = L.col;
@@ -613,45 +617,48 @@ __global__ void __launch_bounds__(SOLVE_MAX_THREADS, 4) k_solve(SolveLaunch L) {
     c.Qw = Qw;
     for (;;) {
         if (threadIdx.x == 0) {
+            const uint32_t U = L.S * L.Q;
+            const uint32_t nu = blockIdx.x < U ? (U - 1u - blockIdx.x) / gridDim.x + 1u : 0u;
             int pick = -1;
             if (ld_relaxed(&L.hdr->abort_flag)) {
                 pick = -2;
-            } else if (globaltimer_ns() - t_begin > KERNEL_LIMIT_FACTOR * L.timeout_ns) {
+            } else if (globaltimer_ns() - sc.t_begin > KERNEL_LIMIT_FACTOR * L.timeout_ns) {
                 // whole-kernel limit: even a busy block cannot run unbounded
                 set_status(L.hdr, SSSP_ETIMEOUT);
                 atomicExch(&L.hdr->abort_flag, 1u);
                 pick = -2;
             } else {
+                const uint32_t rr = sc.rr;
                 for (uint32_t t = 0; t < nu; ++t) {
                     uint32_t j = rr + t;
                     if (j >= nu) j -= nu;
                     const uint32_t uid = blockIdx.x + j * gridDim.x;
                     if (ld_relaxed(&L.dirty[uid]) != 0u && atomicExch(&L.dirty[uid], 0u) != 0u) {
                         pick = (int)uid;
-                        rr = (j + 1u == nu) ? 0u : j + 1u;
+                        sc.rr = (j + 1u == nu) ? 0u : j + 1u;
                         break;
                     }
                 }
                 if (pick >= 0) {
                     __threadfence();  // doorbell before the inbox scan
-                    if (idle_start) sm.st[ST_IDLE] += globaltimer_ns() - idle_start;
-                    idle_start = 0;
-                    backoff = 32;
+                    if (sc.idle_start) sm.st[ST_IDLE] += globaltimer_ns() - sc.idle_start;
+                    sc.idle_start = 0;
+                    sc.backoff = 32;
                 } else if (ld_relaxed(&L.hdr->pending) == 0ull) {
                     pick = -2;  // nothing queued, nothing in flight: terminated
-                    if (idle_start) sm.st[ST_IDLE] += globaltimer_ns() - idle_start;
+                    if (sc.idle_start) sm.st[ST_IDLE] += globaltimer_ns() - sc.idle_start;
                 } else {
                     const uint64_t now = globaltimer_ns();
-                    if (idle_start == 0) {
-                        idle_start = now;
-                    } else if (now - idle_start > L.timeout_ns) {
+                    if (sc.idle_start == 0) {
+                        sc.idle_start = now;
+                    } else if (now - sc.idle_start > L.timeout_ns) {
                         set_status(L.hdr, SSSP_ETIMEOUT);
                         atomicExch(&L.hdr->abort_flag, 1u);
                         pick = -2;
                     }
                     if (pick == -1) {
-                        __nanosleep(backoff);
-                        if (backoff < 1024u) backoff *= 2u;
+                        __nanosleep(sc.backoff);
+                        if (sc.backoff < 1024u) sc.backoff *= 2u;
                     }
                 }
             }
