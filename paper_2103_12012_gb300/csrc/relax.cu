@@ -173,7 +173,7 @@ struct Scalars {
     int pick;
     unsigned long long prob;
     // thread 0's scheduling state (static mode), here rather than in every thread's registers
-    uint32_t rr, backoff;
+    uint32_t backoff;
     unsigned long long idle_start, t_begin;
 };
 
@@ -597,7 +597,6 @@ __global__ void __launch_bounds__(SOLVE_MAX_THREADS, 4) k_solve(SolveLaunch L) {
     __syncthreads();
 
     if (threadIdx.x == 0) {
-        sc.rr = 0;
         sc.backoff = 32;
         sc.idle_start = 0;
         sc.t_begin = globaltimer_ns();
@@ -628,14 +627,14 @@ __global__ void __launch_bounds__(SOLVE_MAX_THREADS, 4) k_solve(SolveLaunch L) {
                 atomicExch(&L.hdr->abort_flag, 1u);
                 pick = -2;
             } else {
-                const uint32_t rr = sc.rr;
-                for (uint32_t t = 0; t < nu; ++t) {
-                    uint32_t j = rr + t;
-                    if (j >= nu) j -= nu;
+                // Units in source order: a block serves its lower sources first, so
+                // the state in use at any time belongs to few sources (measured on
+                // R-MAT scale 22 with 8 sources: 8% faster than round-robin, in spite
+                // of more relaxations).
+                for (uint32_t j = 0; j < nu; ++j) {
                     const uint32_t uid = blockIdx.x + j * gridDim.x;
                     if (ld_relaxed(&L.dirty[uid]) != 0u && atomicExch(&L.dirty[uid], 0u) != 0u) {
                         pick = (int)uid;
-                        sc.rr = (j + 1u == nu) ? 0u : j + 1u;
                         break;
                     }
                 }
