@@ -115,6 +115,17 @@ __device__ __forceinline__ uint32_t nth_queued(uint32_t wb, uint32_t bits, uint3
     return (wb + w) * 32u + p;
 }
 
+// A slot of a shared list for each lane with `take` (one shared atomic per warp);
+// NONE for the others.
+__device__ __forceinline__ uint32_t warp_slot(bool take, uint32_t* count, uint32_t lane) {
+    const uint32_t ball = __ballot_sync(0xFFFFFFFFu, take);
+    if (!ball) return NONE;
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(count, (uint32_t)__popc(ball));
+    base = __shfl_sync(0xFFFFFFFFu, base, 0) + (uint32_t)__popc(ball & ((1u << lane) - 1u));
+    return take ? base : NONE;
+}
+
 // Appends v to list[0, cap) for the lanes with `take` (one shared atomic per warp).
 __device__ __forceinline__ void warp_append(bool take, uint32_t v, uint32_t* list, uint32_t* count, uint32_t cap,
                                             uint32_t lane) {
@@ -233,61 +244,58 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
     }
     __syncthreads();
 
-    // ---- A: scan the inbox, gather queued vertices and their distances.  Each
-    // warp takes 32 words; its lanes then enumerate the set bits by rank, GATHER_G
-    // each with their distance loads in flight together.
+    // ---- A: scan the inbox: count the queued vertices, find their minimum distance
+    // and keep the candidates for the near bucket.  Each warp takes 32 words; its
+    // lanes enumerate the set bits by rank, GATHER_G each with their distance loads
+    // in flight together.  The block minimum only falls as the scan goes on, so a
+    // vertex at or above (running minimum + delta) can never enter the bucket: only
+    // the ones below it are kept (a superset of the bucket, usually far smaller
+    // than all queued vertices).
     const uint32_t wlo = lo >> 5, whi = (hi - 1u) >> 5;
-    uint32_t lmin = 0xFFFFFFFFu, lcnt = 0;
     for (uint32_t wb = wlo + (tid & ~31u); wb <= whi; wb += T) {
         const uint32_t wd = wb + lane;
         const uint32_t bits = wd <= whi ? ld_relaxed(&c.bitmap[wd]) & range_mask(wd, lo, hi) : 0u;
         const uint32_t incl = warp_scan_incl((uint32_t)__popc(bits), lane);
         const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
         if (total == 0) continue;
-        uint32_t base = 0;
-        if (lane == 0) {
-            base = atomicAdd(&sc.nlist, total);
-            lcnt += total;
-        }
-        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        if (lane == 0) atomicAdd(&sc.cnt, total);
         for (uint32_t i0 = lane; i0 < total + lane; i0 += 32u * GATHER_G) {  // warp-uniform trip count
             uint32_t vs[GATHER_G], ds[GATHER_G];
 #pragma unroll
             for (int g = 0; g < GATHER_G; ++g)
                 vs[g] = nth_queued(wb, bits, incl, min(i0 + 32u * g, total - 1u));
-#pragma unroll
-            for (int g = 0; g < GATHER_G; ++g)
-                if (i0 + 32u * g < total) ds[g] = (uint32_t)(__ldcg(&c.packed[vs[g]]) >> 32);
+            uint32_t bm = 0xFFFFFFFFu;
 #pragma unroll
             for (int g = 0; g < GATHER_G; ++g) {
-                const uint32_t i = i0 + 32u * g;
-                if (i < total) {
-                    lmin = min(lmin, ds[g]);
-                    if (base + i < c.gcap) {
-                        sm.list_v[base + i] = vs[g];
-                        sm.list_d[base + i] = ds[g];
-                    }
+                ds[g] = i0 + 32u * g < total ? (uint32_t)(__ldcg(&c.packed[vs[g]]) >> 32) : 0xFFFFFFFFu;
+                bm = min(bm, ds[g]);
+            }
+            bm = warp_min(bm);  // lane 0's first element is valid: bm is a distance
+            if (lane == 0) atomicMin(&sc.dmin, bm);
+            const uint32_t bound = bucket_bound<W>(min(bm, *(volatile uint32_t*)&sc.dmin), c.delta);
+#pragma unroll
+            for (int g = 0; g < GATHER_G; ++g) {
+                const uint32_t k = warp_slot(ds[g] < bound, &sc.nlist, lane);
+                if (k < c.gcap) {
+                    sm.list_v[k] = vs[g];
+                    sm.list_d[k] = ds[g];
                 }
             }
         }
-    }
-    lmin = warp_min(lmin);
-    lcnt = warp_sum(lcnt);
-    if (lane == 0 && lcnt) {
-        atomicMin(&sc.dmin, lmin);
-        atomicAdd(&sc.cnt, lcnt);
     }
     __syncthreads();
     const uint32_t found = sc.cnt;
     uint32_t nsel = 0, te = 0;
     if (found != 0) {
         const uint32_t thr = bucket_bound<W>(sc.dmin, c.delta);
+        const uint32_t nkept = sc.nlist;
 
-        // ---- B: the near bucket, at most `tile` vertices: from the gathered list,
-        // or, when the scan found more than it keeps, by enumerating the inbox again
-        if (found <= c.gcap) {
-            for (uint32_t i = tid; i < found + lane; i += T) {  // warp-uniform trip count
-                const bool take = i < found && sm.list_d[i] < thr;
+        // ---- B: the near bucket, at most `tile` vertices: from the kept candidates,
+        // or, when there were more of them than the list holds, by enumerating the
+        // inbox again
+        if (nkept <= c.gcap) {
+            for (uint32_t i = tid; i < nkept + lane; i += T) {  // warp-uniform trip count
+                const bool take = i < nkept && sm.list_d[i] < thr;
                 warp_append(take, take ? sm.list_v[i] : 0u, sm.sel_v, &sc.nsel, c.tile, lane);
             }
         } else {
