@@ -202,7 +202,8 @@ sssp_status sssp_solve(const sssp_graph* g, const uint32_t* sources, uint32_t S,
  * Autotuner for sssp_solve (the paper has no tuner; its knobs are the process
  * count and the termination timeout).  Runs sssp_solve on (g, sources) with
  * candidate schedules and returns the fastest: the bucket width delta is
- * searched over {1/64 .. 4} x the mean of a sample of the weights, then tile
+ * searched over {1/64 .. 4} x the mean of a sample of the weights (powers of
+ * two), refined at 3/4 and 3/2 of the best of those, then tile
  * over {1024, 2048, 4096}, then split over {1, 2, 4} (split only where ws is
  * large enough).  Each candidate runs `trials` times (>= 1) after one
  * warm-up, timed with CUDA events on `stream`; candidates that fail are

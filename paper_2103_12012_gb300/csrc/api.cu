@@ -271,6 +271,18 @@ sssp_status sssp_autotune(const sssp_graph* g, const uint32_t* sources, uint32_t
             cur = o;
         }
     }
+    // refine the bucket width between the coarse steps
+    const double coarse = cur.delta;
+    for (double f : {0.75, 1.5}) {
+        sssp_options o = cur;
+        o.delta = g->wtype == SSSP_W_F32 ? coarse * f : std::max(1.0, std::floor(coarse * f));
+        if (o.delta == coarse) continue;
+        const float ms = run(o);
+        if (ms < cur_ms) {
+            cur_ms = ms;
+            cur = o;
+        }
+    }
     for (uint32_t tile : {1024u, 2048u, 4096u}) {
         sssp_options o = cur;
         o.tile = tile;
