@@ -359,30 +359,48 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
             __syncthreads();
             const bool last = sub + 1u >= MAX_SUBROUNDS;
 
-            // ---- E: relax all out-edges, edge-parallel.  Each thread takes
-            // EDGE_BATCH consecutive edges (one search of the degree prefix, then
-            // steps over row ends) and keeps them in flight together: all CSR
-            // loads, then all read-first filters, then all atomics.
+            // ---- E: relax all out-edges, edge-parallel.  Each thread keeps
+            // EDGE_BATCH edges in flight together: all CSR loads, then all read-first
+            // filters, then all atomics.  Its edges are a block-width apart (lanes read
+            // consecutive edges: coalesced across short rows) unless the taken vertices
+            // average 32 edges or more (hubs), where a thread takes consecutive edges and
+            // one search of the degree prefix serves all of them.  Row of edge k: the
+            // largest a < nsel with sel_pref[a] <= k (binary lifting, the batch's
+            // searches interleaved).
             uint32_t lact = 0, bad = 0;
             uint32_t n_ai = 0, n_rem = 0;  // statistics: atomics | improved << 16, remote activations
-            for (uint32_t k0 = tid * EDGE_BATCH; k0 < te; k0 += EDGE_BATCH * T) {
+            const bool consec = te >= 32u * nsel;
+            const uint32_t kstep = consec ? 1u : T;
+            const uint32_t top = nsel > 1u ? 1u << (31 - __clz(nsel - 1u)) : 0u;
+            for (uint32_t k0 = consec ? tid * EDGE_BATCH : tid; k0 < te; k0 += EDGE_BATCH * T) {
                 uint32_t vv[EDGE_BATCH], cc[EDGE_BATCH], aa[EDGE_BATCH];
-                uint32_t a = 0, b = nsel;  // sel_pref[a] <= k0 < sel_pref[b]
-                while (b - a > 1u) {
-                    const uint32_t m = (a + b) >> 1;
-                    if (sm.sel_pref[m] <= k0)
-                        a = m;
-                    else
-                        b = m;
+#pragma unroll
+                for (int j = 0; j < EDGE_BATCH; ++j) aa[j] = 0;
+                if (consec) {
+                    for (uint32_t st = top; st; st >>= 1)
+                        if (aa[0] + st < nsel && sm.sel_pref[aa[0] + st] <= k0) aa[0] += st;
+#pragma unroll
+                    for (int j = 1; j < EDGE_BATCH; ++j) {  // step over row ends; sel_pref[nsel] = te
+                        uint32_t a = aa[j - 1];
+                        while (a + 1u < nsel && sm.sel_pref[a + 1u] <= k0 + (uint32_t)j) ++a;
+                        aa[j] = a;
+                    }
+                } else {
+                    for (uint32_t st = top; st; st >>= 1) {
+#pragma unroll
+                        for (int j = 0; j < EDGE_BATCH; ++j) {
+                            const uint32_t m = aa[j] + st;
+                            if (m < nsel && sm.sel_pref[m] <= k0 + (uint32_t)j * T) aa[j] = m;
+                        }
+                    }
                 }
 #pragma unroll
                 for (int j = 0; j < EDGE_BATCH; ++j) {
-                    const uint32_t k = k0 + (uint32_t)j;
+                    const uint32_t k = k0 + (uint32_t)j * kstep;
                     vv[j] = NONE;
                     if (k < te) {
-                        while (sm.sel_pref[a + 1u] <= k) ++a;  // sel_pref[nsel] = te > k ends it
+                        const uint32_t a = aa[j];
                         const uint32_t e = sm.list_v[a] + (k - sm.sel_pref[a]);
-                        aa[j] = a;
                         vv[j] = __ldg(&c.col[e]);
                         cc[j] = __ldg(&c.w[e]);  // the weight, until it becomes the candidate below
                     }
