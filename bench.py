@@ -196,6 +196,13 @@ def run_ours(a):
     prune_ms = e0.elapsed_time(e1)
     pruned = int((keep == 0).sum().item())
     del keep
+    # locality layout: vertices renumbered inside their partitions by degree (one-time); the
+    # solves below run on it and take / return the caller's ids
+    e0.record()
+    h = sssp.layout(g)
+    e1.record()
+    torch.cuda.synchronize()
+    layout_ms = e0.elapsed_time(e1)
 
     sources_d = torch.from_numpy(srcs.view(np.int32)).to(dev)
     tuned_ms = None
@@ -203,9 +210,9 @@ def run_ours(a):
         opts = sssp.options(threads=a.threads, tile=a.tile, delta=a.delta, split=a.split)
     else:
         t0 = time.perf_counter()
-        opts, tuned_ms = sssp.autotune(g, sources_d)
+        opts, tuned_ms = sssp.autotune(h, sources_d)
         tune_s = time.perf_counter() - t0
-    solver = sssp.Solver(g, S, opts)
+    solver = sssp.Solver(h, S, opts)
 
     # warm-up (also the step whose output defines the traversed-edge count)
     for _ in range(max(a.warmup, 1)):
@@ -268,7 +275,7 @@ def run_ours(a):
     # end to end through the C ABI with host buffers
     e2e = None
     if not a.no_e2e:
-        e2e = run_e2e(sssp, g, srcs, opts, dev, E_r, max(3, min(a.steps, 10)))
+        e2e = run_e2e(sssp, h, srcs, opts, dev, E_r, max(3, min(a.steps, 10)))
 
     # CPU baseline: the oracle on this host's cores (rank 0, N=1 only)
     cpu = None
@@ -283,6 +290,8 @@ def run_ours(a):
                                f"{g0.V} vertices, {g0.E_raw} raw edges ({g.E} after dedupe), "
                                f"{S} sources per GPU, {P} partitions",
                    "partitions": P, "sources_per_gpu": S, "l2": "inputs larger than L2 (CSR and state > 0.5 GB)",
+                   "layout": "vertices renumbered inside their partitions by degree (sssp_layout, one-time); "
+                             "sources and outputs in the generator's ids",
                    "options": {"threads": opts.threads or 512, "tile": opts.tile or 1024,
                                "delta": opts.delta or 4, "split": opts.split or 1,
                                "autotuned": not (a.no_tune or a.threads or a.tile or a.delta or a.split)}},
@@ -295,6 +304,7 @@ def run_ours(a):
         "clocks": clk,
         "gpu_launches": 4 * a.steps,
         "phases": {"csr_build_ms": round(csr_ms, 3), "partition_ms": round(part_ms, 3),
+                   "layout_ms": round(layout_ms, 3),
                    "prune_local_ms": round(prune_ms, 3), "pruned_edges": pruned, "edges": g.E,
                    "toka_threshold_interedges": inter_total, "toka_threshold_msgs": inter_total * P},
         "work": {"reached_edges": E_r, "reached_vertices": V_r, "stats_last_step": stats,
@@ -309,27 +319,25 @@ def run_ours(a):
 
 
 def run_e2e(sssp, g, srcs, opts, dev, E_r, steps):
-    """H2D (pinned CSR + sources) -> sssp_solve -> D2H (dist, pred), per step."""
+    """H2D (pinned CSR [+ layout ids] + sources) -> sssp_solve -> D2H (dist, pred), per step."""
     import torch
-    rp_h = g.row_ptr.cpu().pin_memory()
-    col_h = g.col.cpu().pin_memory()
-    w_h = g.w.cpu().pin_memory()
+    host = [g.row_ptr, g.col, g.w] + ([g.ids, g.slots] if g.ids is not None else [])
+    host = [t.cpu().pin_memory() for t in host]
+    devs = [torch.empty_like(t, device=dev) for t in host]
     src_h = torch.from_numpy(srcs.view(np.int32)).pin_memory()
     S = len(srcs)
-    rp_d, col_d, w_d = torch.empty_like(rp_h, device=dev), torch.empty_like(col_h, device=dev), \
-        torch.empty_like(w_h, device=dev)
     src_d = torch.empty_like(src_h, device=dev)
-    gd = sssp.DeviceGraph(g.V, g.E, rp_d, col_d, w_d, g.wtype, g.partitions)
+    gd = sssp.DeviceGraph(g.V, g.E, devs[0], devs[1], devs[2], g.wtype, g.partitions, None,
+                          *(devs[3:5] if len(devs) == 5 else (None, None)))
     solver = sssp.Solver(gd, S, opts)
     dist_h = torch.empty((S, g.V), dtype=torch.int32).pin_memory()
     pred_h = torch.empty((S, g.V), dtype=torch.int32).pin_memory()
-    h2d = rp_h.numel() * 4 + col_h.numel() * 4 + w_h.numel() * 4 + src_h.numel() * 4
+    h2d = sum(t.numel() * 4 for t in host) + src_h.numel() * 4
     d2h = 2 * S * g.V * 4
 
     def step():
-        rp_d.copy_(rp_h, non_blocking=True)
-        col_d.copy_(col_h, non_blocking=True)
-        w_d.copy_(w_h, non_blocking=True)
+        for d_, h_ in zip(devs, host):
+            d_.copy_(h_, non_blocking=True)
         src_d.copy_(src_h, non_blocking=True)
         solver.launch(src_d)
         dist_h.copy_(solver.dist, non_blocking=True)

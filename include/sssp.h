@@ -76,6 +76,14 @@ typedef struct {
     const void* w;           /* device [E], uint32 or float32 according to wtype */
     int32_t wtype;           /* sssp_wtype */
     uint32_t partitions;     /* P >= 1 (Sec. III.A 1D block partitioning) */
+    /* A graph from sssp_layout (both set) or a graph in the caller's own ids (both NULL).
+     * For sssp_solve / sssp_autotune / sssp_solve_noalloc on a layout graph, sources
+     * are given, and dist / pred are written, in the caller's ids, with the same values
+     * (canonical predecessors included) as on the original graph.  sssp_partition,
+     * sssp_prune and sssp_compact work on the CSR as stored; sssp_backward rejects a
+     * layout graph (SSSP_EINVAL). */
+    const uint32_t* ids;     /* device [V] or NULL: caller's id of stored vertex v */
+    const uint32_t* slots;   /* device [V] or NULL: stored vertex of caller's id i (inverse of ids) */
 } sssp_graph;
 
 /* Tuning knobs; a zero field means "default".  None of them changes the
@@ -139,6 +147,32 @@ size_t sssp_build_csr_workspace_size(uint32_t V, uint64_t E_raw);
 sssp_status sssp_build_csr(uint32_t V, uint64_t E_raw, const uint32_t* src, const uint32_t* dst, const void* w,
                            int32_t wtype, uint32_t* row_ptr, uint32_t* col, void* w_out, uint32_t* eid,
                            uint32_t* E_out, void* ws, size_t ws_bytes, sssp_stream_t stream);
+
+/* ------------------------------------------------------- K1b locality layout */
+
+/* Workspace bytes of sssp_layout for graph g (0 if g is invalid or already a layout graph). */
+size_t sssp_layout_workspace_size(const sssp_graph* g);
+
+/*
+ * The same graph with its vertices renumbered inside each 1D block partition
+ * (Sec. III.A: partition membership, hence every partition's vertex count and
+ * inter-edges, is unchanged): within a partition, by total degree (in + out)
+ * descending, ties by the caller's id ascending.  The vertices most relaxations
+ * reach then share cache sectors, which keeps more of the per-source distance
+ * state in L2 during sssp_solve.  The paper has no such step: it only renames
+ * vertices (a layout of the state in memory), and a solve on the result returns
+ * exactly what it returns on g.
+ *   g        : a graph in the caller's ids (g->ids == NULL), rows sorted as sssp_build_csr makes them
+ *   row_ptr_out, col_out, w_out : device [V+1], [E], [E] out: the renumbered CSR (rows sorted)
+ *   emap_out : device [E] out (may be NULL): index in g of stored edge k
+ *   ids_out, slots_out : device [V] out: the sssp_graph ids / slots of the result
+ *   ws       : device workspace >= sssp_layout_workspace_size(g); holds the status word
+ * The result is the sssp_graph {V, E, row_ptr_out, col_out, w_out, wtype, partitions,
+ * ids_out, slots_out}.
+ */
+sssp_status sssp_layout(const sssp_graph* g, uint32_t* row_ptr_out, uint32_t* col_out, void* w_out,
+                        uint32_t* emap_out, uint32_t* ids_out, uint32_t* slots_out, void* ws, size_t ws_bytes,
+                        sssp_stream_t stream);
 
 /* ------------------------------------------------------------ K2 partition */
 

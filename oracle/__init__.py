@@ -12,6 +12,8 @@ other than itself are in ``tests/test_oracle_pins.py``.
 Status of each function's parity pin:
   csr, partition, dijkstra (u32 and f32), trishla, tree_grad -- pinned
   (brute force, library routines, closed forms, finite differences).
+  layout -- pinned (a hand-worked order; brute-force order properties;
+  distances invariant under the renaming).
 """
 from __future__ import annotations
 
@@ -177,3 +179,22 @@ def compact(g: CSR, keep: np.ndarray) -> CSR:
     row_ptr = np.zeros(g.V + 1, np.uint32)
     row_ptr[1:] = np.cumsum(kept_deg)
     return CSR(g.V, row_ptr, g.col[keep].copy(), g.w[keep].copy(), g.eid[keep].copy())
+
+
+def layout(g: CSR, P: int):
+    """The locality layout (a renaming of vertices; the paper has no such step): inside each
+    1D block partition of Sec. III.A (B = ceil(V/P)), vertices ordered by total degree
+    (in + out) descending, ties by id ascending.  Returns (ids, slots, h): ids[n] = old id of
+    new vertex n, slots = its inverse, h = the renamed graph as a canonical CSR whose eid maps
+    each edge to its index in g."""
+    V = g.V
+    deg = np.diff(g.row_ptr.astype(np.int64)) + np.bincount(g.col.astype(np.int64), minlength=V)
+    v = np.arange(V, dtype=np.int64)
+    part = v // (-(-V // P))
+    ids = np.lexsort((v, -deg, part)).astype(np.uint32)  # primary: partition, then degree desc, then id
+    slots = np.empty(V, np.uint32)
+    slots[ids] = np.arange(V, dtype=np.uint32)
+    tails = np.repeat(np.arange(V, dtype=np.uint32), np.diff(g.row_ptr.astype(np.int64)))
+    h = csr(V, slots[tails], slots[g.col], g.w)
+    return ids, slots, h
+

@@ -31,7 +31,7 @@ u32, u64, i32, sz = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32, ctypes.c_s
 
 class SsspGraph(ctypes.Structure):
     _fields_ = [("V", u32), ("E", u32), ("row_ptr", P), ("col", P), ("w", P), ("wtype", i32),
-                ("partitions", u32)]
+                ("partitions", u32), ("ids", P), ("slots", P)]
 
 
 class SsspOptions(ctypes.Structure):
@@ -63,6 +63,8 @@ _SIGS = {
     "sssp_version": (ctypes.c_char_p, []),
     "sssp_build_csr_workspace_size": (sz, [u32, u64]),
     "sssp_build_csr": (i32, [u32, u64, P, P, P, i32, P, P, P, P, P, P, sz, P]),
+    "sssp_layout_workspace_size": (sz, [P]),
+    "sssp_layout": (i32, [P, P, P, P, P, P, P, P, sz, P]),
     "sssp_partition": (i32, [P, P, P, P]),
     "sssp_prune": (i32, [P, i32, P, P, P]),
     "sssp_compact_workspace_size": (sz, [u32, u32]),
@@ -148,13 +150,18 @@ class DeviceGraph:
     w: object  # int32 (uint32 bits) or float32
     wtype: int
     partitions: int = 1
-    eid: object = None  # kept edge -> index in the input edge list
+    eid: object = None  # kept edge -> index in the input edge list (for a layout graph: in the graph it came from)
+    ids: object = None  # layout graph: stored vertex -> caller's id
+    slots: object = None  # layout graph: caller's id -> stored vertex
 
     def c(self) -> SsspGraph:
         return SsspGraph(self.V, self.E, self.row_ptr.data_ptr(), self.col.data_ptr() if self.E else None,
-                         self.w.data_ptr() if self.E else None, self.wtype, self.partitions)
+                         self.w.data_ptr() if self.E else None, self.wtype, self.partitions,
+                         _ptr(self.ids), _ptr(self.slots))
 
     def with_partitions(self, P):
+        if self.ids is not None:
+            raise ValueError("a layout graph keeps the partitions it was made for")
         return DeviceGraph(self.V, self.E, self.row_ptr, self.col, self.w, self.wtype, P, self.eid)
 
 
@@ -202,6 +209,30 @@ def upload_csr(V, row_ptr, col, w, partitions=1, eid=None) -> DeviceGraph:
     E = int(np.asarray(row_ptr)[-1])
     return DeviceGraph(V, E, _as_dev_u32(np.asarray(row_ptr, np.uint32)), _as_dev_u32(np.asarray(col, np.uint32)),
                        w_d, wt, partitions, None if eid is None else _as_dev_u32(np.asarray(eid, np.uint32)))
+
+
+def layout(g: DeviceGraph, stream=None) -> DeviceGraph:
+    """sssp_layout: g with its vertices renumbered inside each block partition by degree (a
+    memory layout for the solve; solves on the result take and return the caller's ids)."""
+    torch = _torch()
+    row_ptr = torch.empty(g.V + 1, dtype=torch.int32, device="cuda")
+    col = torch.empty(max(g.E, 1), dtype=torch.int32, device="cuda")
+    w = torch.empty(max(g.E, 1), dtype=g.w.dtype, device="cuda")
+    emap = torch.empty(max(g.E, 1), dtype=torch.int32, device="cuda")
+    ids = torch.empty(g.V, dtype=torch.int32, device="cuda")
+    slots = torch.empty(g.V, dtype=torch.int32, device="cuda")
+    L = lib()
+    gc = g.c()
+    nb = L.sssp_layout_workspace_size(ctypes.byref(gc))
+    if nb == 0:
+        raise SsspError(SSSP_EINVAL, "sssp_layout_workspace_size")
+    ws = _ws(nb)
+    st = _stream(stream)
+    _check(L.sssp_layout(ctypes.byref(gc), _ptr(row_ptr), _ptr(col), _ptr(w), _ptr(emap), _ptr(ids), _ptr(slots),
+                         _ptr(ws), nb, st), "sssp_layout")
+    _check(L.sssp_workspace_status(_ptr(ws), st, None), "sssp_layout (device)")
+    return DeviceGraph(g.V, g.E, row_ptr, col[:max(g.E, 1)], w[:max(g.E, 1)], g.wtype, g.partitions,
+                       emap[:max(g.E, 1)], ids, slots)
 
 
 def partition(g: DeviceGraph, stream=None):
@@ -295,7 +326,7 @@ def _graph_class(g: DeviceGraph, S: int) -> str:
     """Cache key: sizes, weight type, partitions, sources and the weight scale (mean of a sample)."""
     wm = float(g.w[:min(g.E, 65536)].float().mean().item()) if g.E and g.wtype == W_F32 else (
         float((g.w[:min(g.E, 65536)].long() & 0xFFFFFFFF).double().mean().item()) if g.E else 0.0)
-    return f"V{g.V}:E{g.E}:w{g.wtype}:P{g.partitions}:S{S}:m{wm:.3g}"
+    return f"V{g.V}:E{g.E}:w{g.wtype}:P{g.partitions}:S{S}:m{wm:.3g}" + (":layout" if g.ids is not None else "")
 
 
 def autotune(g: DeviceGraph, sources, base: SsspOptions | None = None, trials: int = 1, cache: bool = True):
@@ -349,6 +380,8 @@ class Batch:
         sources: list of source arrays, one per graph."""
         torch = _torch()
         self.opts = opts or options()
+        if any(getattr(g, "ids", None) is not None for g in graphs):
+            raise ValueError("batched solves take graphs in the caller's ids, not layout graphs")
         Vs = [int(g.V) for g in graphs]
         self.row_off = np.concatenate([[0], np.cumsum([v + 1 for v in Vs])[:-1]]).astype(np.uint64)
         if isinstance(graphs[0], DeviceGraph):

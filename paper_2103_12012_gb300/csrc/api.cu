@@ -35,6 +35,7 @@ bool graph_ok(const sssp_graph* g) {
     if (!g || g->V == 0 || g->partitions == 0 || g->partitions > g->V) return false;
     if (!g->row_ptr || (g->E && (!g->col || !g->w))) return false;
     if (g->wtype != SSSP_W_U32 && g->wtype != SSSP_W_F32) return false;
+    if ((g->ids == nullptr) != (g->slots == nullptr)) return false;
     return true;
 }
 
@@ -132,6 +133,21 @@ sssp_status sssp_build_csr(uint32_t V, uint64_t E_raw, const uint32_t* src, cons
                      static_cast<uint32_t*>(w_out), eid, E_out, ws, ws_bytes, (cudaStream_t)stream);
 }
 
+size_t sssp_layout_workspace_size(const sssp_graph* g) {
+    if (!graph_ok(g) || g->ids) return 0;
+    return layout_workspace_bytes(g->V, g->E);
+}
+
+sssp_status sssp_layout(const sssp_graph* g, uint32_t* row_ptr_out, uint32_t* col_out, void* w_out,
+                        uint32_t* emap_out, uint32_t* ids_out, uint32_t* slots_out, void* ws, size_t ws_bytes,
+                        sssp_stream_t stream) {
+    if (!graph_ok(g) || g->ids || !row_ptr_out || !ids_out || !slots_out || !ws || !aligned16(ws)) return SSSP_EINVAL;
+    if (g->E && (!col_out || !w_out)) return SSSP_EINVAL;
+    if (ws_bytes < layout_workspace_bytes(g->V, g->E)) return SSSP_ENOMEM;
+    return layout_build(g, row_ptr_out, col_out, static_cast<uint32_t*>(w_out), emap_out, ids_out, slots_out, ws,
+                        ws_bytes, (cudaStream_t)stream);
+}
+
 sssp_status sssp_partition(const sssp_graph* g, uint32_t* bounds, uint64_t* inter, sssp_stream_t stream) {
     if (!graph_ok(g) || !bounds) return SSSP_EINVAL;
     return partition_launch(g, bounds, inter, (cudaStream_t)stream) == cudaSuccess ? SSSP_OK : SSSP_ECUDA;
@@ -179,6 +195,8 @@ sssp_status sssp_solve(const sssp_graph* g, const uint32_t* sources, uint32_t S,
     l.w = static_cast<const uint32_t*>(g->w);
     l.wtype = g->wtype;
     l.V = g->V;
+    l.ids = g->ids;
+    l.slots = g->slots;
     l.S = S;
     l.sources = sources;
     l.B = L.B;
@@ -491,7 +509,7 @@ size_t sssp_backward_workspace_size(uint32_t V, uint32_t E, uint32_t S) { return
 
 sssp_status sssp_backward(const sssp_graph* g, uint32_t S, const uint32_t* pred, const float* grad_dist,
                           float* grad_w, void* ws, size_t ws_bytes, sssp_stream_t stream) {
-    if (!graph_ok(g) || S == 0 || !pred || !grad_dist || (g->E && !grad_w) || !ws) return SSSP_EINVAL;
+    if (!graph_ok(g) || g->ids || S == 0 || !pred || !grad_dist || (g->E && !grad_w) || !ws) return SSSP_EINVAL;
     if (ws_bytes < backward_workspace_bytes(g->V, g->E, S)) return SSSP_ENOMEM;
     return backward_launch(g, S, pred, grad_dist, grad_w, ws, (cudaStream_t)stream) == cudaSuccess ? SSSP_OK
                                                                                                   : SSSP_ECUDA;

@@ -216,6 +216,53 @@ __global__ void k_compact(uint32_t V, uint32_t E, const uint32_t* __restrict__ r
     if (gtid == 0) *E_out = E ? pos[E - 1] : 0u;
 }
 
+// ---- locality layout: renumber vertices inside each block partition by degree
+
+__global__ void k_lay_deg(uint32_t V, const uint32_t* __restrict__ row_ptr, uint32_t* deg) {
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x)
+        deg[v] = row_ptr[v + 1] - row_ptr[v];
+}
+
+__global__ void k_lay_indeg(uint32_t V, uint32_t E, const uint32_t* __restrict__ col, uint32_t* deg) {
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
+        const uint32_t v = col[e];
+        if (v < V) atomicAdd(&deg[v], 1u);
+    }
+}
+
+// key = (partition << 32) | ~degree: an ascending stable sort gives partitions in
+// order, each by degree descending, ties by id ascending (the values start in id order)
+__global__ void k_lay_keys(uint32_t V, unsigned long long B, const uint32_t* __restrict__ deg,
+                           unsigned long long* keys, uint32_t* vals) {
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x) {
+        keys[v] = ((unsigned long long)(v / B) << 32) | (0xFFFFFFFFu - deg[v]);
+        vals[v] = v;
+    }
+}
+
+__global__ void k_lay_slots(uint32_t V, const uint32_t* __restrict__ order, uint32_t* ids, uint32_t* slots) {
+    for (uint32_t n = blockIdx.x * blockDim.x + threadIdx.x; n < V; n += gridDim.x * blockDim.x) {
+        const uint32_t v = order[n];
+        ids[n] = v;
+        slots[v] = n;
+    }
+}
+
+// one warp per stored row: the edge list in the new numbering, in the old edge order
+__global__ void k_lay_coo(uint32_t V, const uint32_t* __restrict__ row_ptr, const uint32_t* __restrict__ col,
+                          const uint32_t* __restrict__ slots, uint32_t* src, uint32_t* dst) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t u = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < V; u += warps) {
+        const uint32_t beg = row_ptr[u], end = row_ptr[u + 1], su = slots[u];
+        for (uint32_t e = beg + lane; e < end; e += 32u) {
+            src[e] = su;
+            const uint32_t v = col[e];
+            dst[e] = v < V ? slots[v] : 0xFFFFFFFFu;  // a bad head stays bad: the CSR builder reports it
+        }
+    }
+}
+
 unsigned grid_for(uint64_t n, unsigned threads = 256) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -277,6 +324,80 @@ cudaError_t partition_launch(const sssp_graph* g, uint32_t* bounds, uint64_t* in
     k_partition<<<blocks, 256, 0, st>>>(g->V, g->partitions, B, g->row_ptr, g->col, bounds,
                                         reinterpret_cast<unsigned long long*>(inter));
     return cudaGetLastError();
+}
+
+namespace {
+struct LayoutWs {
+    size_t off_deg, off_kin, off_kout, off_vin, off_vout, off_cub, off_src, off_dst, off_eout, total;
+    size_t csr_bytes, cub_bytes;
+};
+
+LayoutWs layout_ws(uint32_t V, uint32_t E) {
+    LayoutWs w{};
+    w.csr_bytes = csr_workspace_bytes(V, E);
+    size_t a = 0;
+    cub::DeviceRadixSort::SortPairs(nullptr, a, (unsigned long long*)nullptr, (unsigned long long*)nullptr,
+                                    (uint32_t*)nullptr, (uint32_t*)nullptr, (int64_t)V, 0, 64);
+    w.cub_bytes = a;
+    size_t off = align_up(w.csr_bytes, 256);  // the CSR builder's workspace first: its header is the status word
+    auto take = [&](size_t bytes) {
+        const size_t r = off;
+        off += align_up(std::max<size_t>(bytes, 4), 256);
+        return r;
+    };
+    w.off_deg = take(4ull * V);
+    w.off_kin = take(8ull * V);
+    w.off_kout = take(8ull * V);
+    w.off_vin = take(4ull * V);
+    w.off_vout = take(4ull * V);
+    w.off_cub = take(w.cub_bytes);
+    w.off_src = take(4ull * E);
+    w.off_dst = take(4ull * E);
+    w.off_eout = take(4);
+    w.total = off;
+    return w;
+}
+}  // namespace
+
+size_t layout_workspace_bytes(uint32_t V, uint32_t E) { return layout_ws(V, E).total; }
+
+sssp_status layout_build(const sssp_graph* g, uint32_t* row_ptr_out, uint32_t* col_out, uint32_t* w_out,
+                         uint32_t* emap_out, uint32_t* ids_out, uint32_t* slots_out, void* ws, size_t ws_bytes,
+                         cudaStream_t st) {
+    const LayoutWs L = layout_ws(g->V, g->E);
+    if (ws_bytes < L.total) return SSSP_ENOMEM;
+    char* p = static_cast<char*>(ws);
+    uint32_t* deg = reinterpret_cast<uint32_t*>(p + L.off_deg);
+    unsigned long long* kin = reinterpret_cast<unsigned long long*>(p + L.off_kin);
+    unsigned long long* kout = reinterpret_cast<unsigned long long*>(p + L.off_kout);
+    uint32_t* vin = reinterpret_cast<uint32_t*>(p + L.off_vin);
+    uint32_t* vout = reinterpret_cast<uint32_t*>(p + L.off_vout);
+    uint32_t* src = reinterpret_cast<uint32_t*>(p + L.off_src);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(p + L.off_dst);
+    uint32_t* eout = reinterpret_cast<uint32_t*>(p + L.off_eout);
+    const unsigned long long B = ((unsigned long long)g->V + g->partitions - 1) / g->partitions;
+    const unsigned gv = grid_for(g->V), ge = grid_for(std::max<uint32_t>(g->E, 1));
+    k_lay_deg<<<gv, 256, 0, st>>>(g->V, g->row_ptr, deg);
+    CK(cudaGetLastError());
+    if (g->E) {
+        k_lay_indeg<<<ge, 256, 0, st>>>(g->V, g->E, g->col, deg);
+        CK(cudaGetLastError());
+    }
+    k_lay_keys<<<gv, 256, 0, st>>>(g->V, B, deg, kin, vin);
+    CK(cudaGetLastError());
+    size_t tb = L.cub_bytes;
+    CK(cub::DeviceRadixSort::SortPairs(p + L.off_cub, tb, kin, kout, vin, vout, (int64_t)g->V, 0,
+                                       32 + (int)bits_for(g->partitions - 1u), st));
+    k_lay_slots<<<gv, 256, 0, st>>>(g->V, vout, ids_out, slots_out);
+    CK(cudaGetLastError());
+    if (g->E) {
+        k_lay_coo<<<grid_for((uint64_t)g->V * 32), 256, 0, st>>>(g->V, g->row_ptr, g->col, slots_out, src, dst);
+        CK(cudaGetLastError());
+    }
+    // the renumbered edge list through the CSR builder: rows sorted by new head id, and
+    // its input-index output maps each stored edge back to its index in g
+    return csr_build(g->V, g->E, src, dst, static_cast<const uint32_t*>(g->w), g->wtype, row_ptr_out, col_out, w_out,
+                     emap_out, eout, ws, L.csr_bytes, st);
 }
 
 size_t compact_workspace_bytes(uint32_t V, uint32_t E) {

@@ -19,6 +19,8 @@ struct SolveLaunch {
     const uint32_t* w;
     int wtype;
     uint32_t V;
+    const uint32_t* ids;    // stored vertex -> caller's id (NULL: identity)
+    const uint32_t* slots;  // caller's id -> stored vertex (NULL: identity)
     // problems
     uint32_t S;
     const uint32_t* sources;
@@ -83,6 +85,10 @@ sssp_status csr_build(uint32_t V, uint64_t E_raw, const uint32_t* src, const uin
                       int wtype, uint32_t* row_ptr, uint32_t* col, uint32_t* w_out, uint32_t* eid, uint32_t* E_out,
                       void* ws, size_t ws_bytes, cudaStream_t st);
 cudaError_t partition_launch(const sssp_graph* g, uint32_t* bounds, uint64_t* inter, cudaStream_t st);
+size_t layout_workspace_bytes(uint32_t V, uint32_t E);
+sssp_status layout_build(const sssp_graph* g, uint32_t* row_ptr_out, uint32_t* col_out, uint32_t* w_out,
+                         uint32_t* emap_out, uint32_t* ids_out, uint32_t* slots_out, void* ws, size_t ws_bytes,
+                         cudaStream_t st);
 size_t compact_workspace_bytes(uint32_t V, uint32_t E);
 sssp_status compact_launch(const sssp_graph* g, const uint8_t* keep, uint32_t* row_ptr_out, uint32_t* col_out,
                            uint32_t* w_out, uint32_t* emap_out, uint32_t* E_out, void* ws, size_t ws_bytes,

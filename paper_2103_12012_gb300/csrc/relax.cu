@@ -197,6 +197,7 @@ struct Ctx {
     const uint32_t* row_ptr;
     const uint32_t* col;
     const uint32_t* w;
+    const uint32_t* ids;  // stored vertex -> caller's id, the predecessor label (NULL: identity)
     uint32_t V;
     unsigned long long* packed;
     uint32_t* bitmap;
@@ -334,6 +335,7 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
                 du = (uint32_t)(__ldcg(&c.packed[u]) >> 32);
                 beg = __ldg(&c.row_ptr[u]);
                 deg = __ldg(&c.row_ptr[u + 1]) - beg;
+                if (c.ids) sm.sel_v[i] = __ldg(&c.ids[u]);  // from here on sel_v holds predecessor labels
             } else {
                 sm.sel_v[i] = NONE;
             }
@@ -491,7 +493,7 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
             // the next sub-round's entries: the queued local vertices with fresh distances
             for (uint32_t i = tid; i < nlq; i += T) {
                 const uint32_t u = sm.lq[i];
-                sm.sel_v[i] = u;
+                sm.sel_v[i] = c.ids ? __ldg(&c.ids[u]) : u;
                 sm.list_d[i] = (uint32_t)(__ldcg(&c.packed[u]) >> 32);
                 const uint32_t beg = __ldg(&c.row_ptr[u]);
                 sm.list_v[i] = beg;
@@ -583,11 +585,12 @@ __global__ void k_seed(SolveLaunch L) {
     const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s == 0 && L.hold_pending) atomicAdd(&L.hdr->pending, 1ull);
     if (s >= L.S) return;
-    const uint32_t src = L.sources[s];
+    uint32_t src = L.sources[s];
     if (src >= L.V) {
         set_status(L.hdr, SSSP_EINVAL);
         return;
     }
+    if (L.slots) src = L.slots[src];  // caller's id -> stored vertex
     L.packed[(size_t)s * L.V + src] = SRC_KEY;
     atomicOr(&L.bitmap[(size_t)s * L.words + (src >> 5)], 1u << (src & 31u));
     const uint32_t p = src / L.B;
@@ -597,12 +600,19 @@ __global__ void k_seed(SolveLaunch L) {
     L.dirty[(size_t)s * L.Q + q] = 1u;
 }
 
+// dist / pred in the caller's ids: element i of source s reads the packed word of
+// stored vertex slots[i] (predecessor labels are caller's ids already).
 template <class W>
-__global__ void k_unpack(const unsigned long long* __restrict__ packed, size_t n, uint32_t* __restrict__ dist,
-                         uint32_t* __restrict__ pred) {
+__global__ void k_unpack(const unsigned long long* __restrict__ packed, size_t n, uint32_t V,
+                         const uint32_t* __restrict__ slots, uint32_t* __restrict__ dist, uint32_t* __restrict__ pred) {
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const unsigned long long k = packed[i];
+        size_t at = i;
+        if (slots) {
+            const size_t s = i / V;
+            at = s * V + __ldg(&slots[i - s * V]);
+        }
+        const unsigned long long k = packed[at];
         dist[i] = k == INF_KEY ? W::inf_out() : (uint32_t)(k >> 32);
         if (pred) pred[i] = k == INF_KEY ? NONE : (uint32_t)k;
     }
@@ -631,6 +641,7 @@ __global__ void __launch_bounds__(SOLVE_MAX_THREADS, 4) k_solve(SolveLaunch L) {
     c.row_ptr = L.row_ptr;
     c.col = L.col;
     c.w = L.w;
+    c.ids = L.ids;
     c.V = L.V;
     c.hdr = L.hdr;
     c.delta = L.delta_bits;
@@ -725,6 +736,7 @@ __global__ void __launch_bounds__(SOLVE_MAX_THREADS, 4) k_batched(BatchLaunch L)
     c.tile = L.tile;
     c.gcap = gather_cap(L.tile);
     c.dirty = nullptr;
+    c.ids = nullptr;
     c.B = c.Bq = c.split = 1u;
     c.Qw = 0;
     const uint32_t T = blockDim.x, tid = threadIdx.x;
@@ -844,9 +856,9 @@ cudaError_t launch_solve(const SolveLaunch& L, cudaStream_t st) {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const unsigned blocks = (unsigned)std::min<size_t>(std::max<size_t>((n_packed + 255) / 256, 1), (size_t)sms * 8);
         if (L.wtype == SSSP_W_F32)
-            k_unpack<WF32><<<blocks, 256, 0, st>>>(L.packed, n_packed, L.dist, L.pred);
+            k_unpack<WF32><<<blocks, 256, 0, st>>>(L.packed, n_packed, L.V, L.slots, L.dist, L.pred);
         else
-            k_unpack<WU32><<<blocks, 256, 0, st>>>(L.packed, n_packed, L.dist, L.pred);
+            k_unpack<WU32><<<blocks, 256, 0, st>>>(L.packed, n_packed, L.V, L.slots, L.dist, L.pred);
     }
     return cudaGetLastError();
 }

@@ -92,3 +92,25 @@ def test_batch_tables_checked_on_host(L):
     assert L.sssp_batch_workspace_size(ctypes.byref(b), None) == 0
     ps[1] = 9
     assert L.sssp_batch_workspace_size(ctypes.byref(b), None) > 0
+
+
+def test_layout_host_checks_without_gpu(L):
+    g = _graph(V=1000, E=5000, P=4)
+    need = L.sssp_layout_workspace_size(ctypes.byref(g))
+    assert need > 5000 * 8 + 1000 * 24  # renumbered edge list + sort keys and values
+    assert L.sssp_layout_workspace_size(None) == 0
+    lay = _graph(V=1000, E=5000, P=4)
+    lay.ids, lay.slots = 16, 16
+    assert L.sssp_layout_workspace_size(ctypes.byref(lay)) == 0  # already a layout graph
+    half = _graph(V=1000, E=5000, P=4)
+    half.ids = 16  # ids without slots: not a graph
+    assert L.sssp_solve_workspace_size(ctypes.byref(half), 1, None) == 0
+    assert L.sssp_solve(ctypes.byref(half), 16, 1, 16, None, None, 16, 1 << 20, None) == sssp.SSSP_EINVAL
+    # missing outputs, misaligned or short workspace
+    assert L.sssp_layout(ctypes.byref(g), None, 16, 16, None, 16, 16, 16, need, None) == sssp.SSSP_EINVAL
+    assert L.sssp_layout(ctypes.byref(g), 16, 16, 16, None, None, 16, 16, need, None) == sssp.SSSP_EINVAL
+    assert L.sssp_layout(ctypes.byref(g), 16, 16, 16, None, 16, 16, 17, need, None) == sssp.SSSP_EINVAL
+    assert L.sssp_layout(ctypes.byref(g), 16, 16, 16, None, 16, 16, 16, need - 1, None) == sssp.SSSP_ENOMEM
+    assert L.sssp_layout(ctypes.byref(lay), 16, 16, 16, None, 16, 16, 16, need, None) == sssp.SSSP_EINVAL
+    # the tree backward indexes edges of the graph it is given: a layout graph is refused
+    assert L.sssp_backward(ctypes.byref(lay), 1, 16, 16, 16, 16, 1 << 30, None) == sssp.SSSP_EINVAL

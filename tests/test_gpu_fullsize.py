@@ -83,6 +83,18 @@ def test_rmat22_eight_sources(sssp):
     assert st == sssp.SSSP_OK
     check_oracle_sources(ref, dist, pred, srcs, [0, len(srcs) - 1])
     check_invariants(g, dist, pred, srcs.tolist())
+    # the benchmark solves on the locality layout: the renaming equals the oracle's, and the
+    # solve on it returns the same distances and canonical predecessors, in the caller's ids
+    h = sssp.layout(g)
+    ids, slots, rh = oracle.layout(ref, P)
+    assert np.array_equal(u32(h.ids), ids) and np.array_equal(u32(h.slots), slots)
+    check_csr_equal(h, rh)
+    assert np.array_equal(u32(h.eid), rh.eid)
+    del rh
+    dist2, pred2, st, _ = sssp.solve(h, srcs)
+    assert st == sssp.SSSP_OK
+    assert torch.equal(dist2, dist) and torch.equal(pred2, pred)
+    check_oracle_sources(ref, dist2, pred2, srcs, [1])
 
 
 def test_grid4096_corner(sssp):

@@ -83,6 +83,60 @@ def test_partition_parity(sssp, V, P):
     assert np.array_equal(inter.cpu().numpy().astype(np.uint64), ri)
 
 
+# ------------------------------------------------------------- locality layout
+
+@pytest.mark.parametrize("seed,V,E,P,f32", [(30, 1000, 20000, 7, False), (31, 5000, 40000, 148, False),
+                                            (32, 777, 9000, 1, True), (33, 64, 0, 4, False),
+                                            (34, 100000, 800000, 148, False), (35, 10, 40, 10, False)])
+def test_layout_parity(sssp, seed, V, E, P, f32):
+    src, dst, w = raw_graph(seed, V, E, f32=f32)
+    ref = oracle.csr(V, src, dst, w)
+    g = sssp.build_csr(V, src, dst, w, partitions=P)
+    h = sssp.layout(g)
+    ids, slots, rh = oracle.layout(ref, P)
+    assert np.array_equal(u32(h.ids), ids) and np.array_equal(u32(h.slots), slots)
+    assert h.E == rh.E and np.array_equal(u32(h.row_ptr), rh.row_ptr)
+    if rh.E:
+        assert np.array_equal(u32(h.col), rh.col)
+        assert np.array_equal(u32(h.w), rh.w.view(np.uint32))
+        assert np.array_equal(u32(h.eid), rh.eid)
+
+
+def test_layout_rmat_skewed_and_partition_counts_unchanged(sssp):
+    g0 = gg.rmat(gg.BASE_SEED + 77, 14, 16 << 14)
+    ref = oracle.csr_of(g0)
+    g = sssp.build_csr(g0.V, g0.src, g0.dst, g0.w, partitions=37)
+    h = sssp.layout(g)
+    ids, slots, _ = oracle.layout(ref, 37)
+    assert np.array_equal(u32(h.ids), ids)
+    # renaming inside partitions keeps every partition's inter-edge count (Sec. III.D's threshold input)
+    b0, i0 = sssp.partition(g)
+    b1, i1 = sssp.partition(h)
+    assert torch.equal(b0, b1) and torch.equal(i0, i1)
+
+
+@pytest.mark.parametrize("seed,V,E,P,f32,split", [(40, 20000, 300000, 148, False, 1), (41, 20000, 300000, 37, False, 2),
+                                                  (42, 5000, 60000, 5, True, 1), (43, 3000, 2000, 3, False, 1)])
+def test_solve_on_layout_graph(sssp, seed, V, E, P, f32, split):
+    src, dst, w = raw_graph(seed, V, E, f32=f32, whi=9)  # narrow weights: many equal-distance ties
+    ref = oracle.csr(V, src, dst, w)
+    g = sssp.build_csr(V, src, dst, w, partitions=P)
+    h = sssp.layout(g)
+    check_solve(sssp, h, ref, [0, 1, V - 1, 12345 % V], sssp.options(split=split))
+
+
+def test_solve_on_layout_rmat(sssp):
+    g0 = gg.rmat(gg.BASE_SEED + 78, 15, 16 << 15)
+    ref = oracle.csr_of(g0)
+    g = sssp.build_csr(g0.V, g0.src, g0.dst, g0.w, partitions=148)
+    h = sssp.layout(g)
+    srcs = gg.pick_sources(gg.BASE_SEED + 78, g0, 4)
+    check_solve(sssp, h, ref, srcs.tolist())
+    with pytest.raises(sssp.SsspError):
+        sssp.backward(h, torch.zeros((1, g0.V), dtype=torch.int32, device="cuda"),
+                      torch.zeros((1, g0.V), device="cuda"))
+
+
 # ------------------------------------------------------------------------ K3
 
 @pytest.mark.parametrize("mode", [0, 1])

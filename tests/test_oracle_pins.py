@@ -339,3 +339,60 @@ def test_tree_grad_vs_central_finite_differences(seed):
                 tree[g.row_ptr[u] + np.searchsorted(g.col[g.row_ptr[u]:g.row_ptr[u + 1]], v)] = True
     assert (grad[~tree] == 0).all()
     assert rows.shape[0] == g.E
+
+
+# ---------------------------------------------------------- locality layout
+
+def test_layout_hand_worked_order():
+    # V = 6, P = 2 (B = 3); total degrees (in + out): 0:2 1:2 2:3 3:2 4:2 5:3
+    src = np.array([0, 0, 1, 3, 5, 5, 2], np.uint32)
+    dst = np.array([1, 2, 2, 4, 3, 4, 5], np.uint32)
+    w = np.array([4, 1, 2, 7, 1, 9, 3], np.uint32)
+    g = oracle.csr(6, src, dst, w)
+    ids, slots, h = oracle.layout(g, 2)
+    assert ids.tolist() == [2, 0, 1, 5, 3, 4]  # each block: degree 3 first, then the degree-2 ids ascending
+    assert slots.tolist() == [1, 2, 0, 4, 5, 3]
+    # edge 0 -> 2 (w 1) becomes 1 -> 0; edge 2 -> 5 (w 3) becomes 0 -> 3
+    row = lambda u: list(zip(h.col[h.row_ptr[u]:h.row_ptr[u + 1]].tolist(), h.w[h.row_ptr[u]:h.row_ptr[u + 1]].tolist()))
+    assert row(1) == [(0, 1), (2, 4)] and row(0) == [(3, 3)]
+
+
+@pytest.mark.parametrize("seed,V,E,P", [(0, 50, 300, 4), (1, 97, 500, 5), (2, 64, 64, 64), (3, 33, 0, 3), (4, 200, 3000, 7)])
+def test_layout_order_properties_brute_force(seed, V, E, P):
+    src, dst, w = _rand_graph(seed, V, E)
+    g = oracle.csr(V, src, dst, w)
+    ids, slots, h = oracle.layout(g, P)
+    B = -(-V // P)
+    deg = [0] * V
+    for u in range(V):
+        for e in range(g.row_ptr[u], g.row_ptr[u + 1]):
+            deg[u] += 1
+            deg[int(g.col[e])] += 1
+    assert sorted(ids.tolist()) == list(range(V))
+    for n in range(V):
+        assert slots[ids[n]] == n
+        assert ids[n] // B == n // B  # same partition
+        if n + 1 < V and (n + 1) // B == n // B:
+            a, b = int(ids[n]), int(ids[n + 1])
+            assert deg[a] > deg[b] or (deg[a] == deg[b] and a < b)
+    # the renamed graph holds exactly the renamed edges, each mapped back by eid
+    want = sorted((int(slots[u]), int(slots[g.col[e]]), int(g.w[e]))
+                  for u in range(V) for e in range(g.row_ptr[u], g.row_ptr[u + 1]))
+    got = []
+    for n in range(V):
+        for k in range(h.row_ptr[n], h.row_ptr[n + 1]):
+            got.append((n, int(h.col[k]), int(h.w[k])))
+            e = int(h.eid[k])
+            assert slots[np.searchsorted(g.row_ptr, e, side="right") - 1] == n and slots[g.col[e]] == h.col[k]
+    assert sorted(got) == want
+
+
+def test_layout_keeps_distances():
+    V, P = 120, 6
+    src, dst, w = _rand_graph(9, V, 900)
+    g = oracle.csr(V, src, dst, w)
+    ids, slots, h = oracle.layout(g, P)
+    for s in (0, 17, 119):
+        d0, _, _ = oracle.dijkstra(g, s)
+        d1, _, _ = oracle.dijkstra(h, int(slots[s]))
+        assert np.array_equal(d1[slots], d0)
