@@ -47,14 +47,9 @@ constexpr uint64_t KERNEL_LIMIT_FACTOR = 3;  // whole-kernel wall-clock limit = 
 constexpr uint32_t MAX_SUBROUNDS = 256;       // local sub-rounds one round may run
 constexpr uint32_t GATHER_MIN = 1024;          // queued vertices one scan can keep (at least)
 constexpr int GATHER_G = 2;                   // queued vertices a lane enumerates and loads together
+constexpr uint32_t IDLE_BACKOFF_MAX_NS = 1024;  // longest sleep of a block with no dirty unit
 constexpr int EDGE_BATCH = 3;                // edges in flight per thread in phase E (measured: 2-4 similar)
 constexpr unsigned long long ROUND_RESERVE = 1ull << 32;  // termination counts reserved per round (> edges)
-
-__device__ __forceinline__ uint32_t atom_or_release(uint32_t* p, uint32_t v) {
-    uint32_t old;
-    asm volatile("atom.release.gpu.global.or.b32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-    return old;
-}
 
 __device__ __forceinline__ uint32_t atom_and_acquire(uint32_t* p, uint32_t v) {
     uint32_t old;
@@ -68,11 +63,6 @@ __device__ __forceinline__ uint32_t warp_min(uint32_t x) {
 }
 
 __device__ __forceinline__ uint32_t warp_sum(uint32_t x) {
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
-    return x;
-}
-
-__device__ __forceinline__ unsigned long long warp_sum64(unsigned long long x) {
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
     return x;
 }
@@ -235,13 +225,7 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
         sc.nclaim = 0;
         sc.act = 0;
         sc.bad = 0;
-        if (STATIC) {
-            // Reserve termination counts before this round can make any inbox bit
-            // visible (a round activates at most one vertex per relaxed edge, fewer
-            // than ROUND_RESERVE); the fence overlaps with the other threads' scan.
-            atomicAdd(&c.hdr->pending, ROUND_RESERVE);
-            __threadfence();
-        }
+        // (static mode: the pick reserved this round's termination counts)
     }
     __syncthreads();
 
@@ -652,38 +636,55 @@ __global__ void __launch_bounds__(SOLVE_MAX_THREADS, 4) k_solve(SolveLaunch L) {
     c.split = L.split;
     c.Qw = Qw;
     for (;;) {
-        if (threadIdx.x == 0) {
+        if (threadIdx.x < 32) {
+            // warp 0 picks: lane 0 checks the limits, the lanes read the block's doorbells
+            // together, and the lowest dirty unit (units in source order: a block serves
+            // its lower sources first, so the state in use at any time belongs to few
+            // sources) is taken with an exchange
+            const uint32_t lane = threadIdx.x;
             const uint32_t U = L.S * L.Q;
             const uint32_t nu = blockIdx.x < U ? (U - 1u - blockIdx.x) / gridDim.x + 1u : 0u;
             int pick = -1;
-            if (ld_relaxed(&L.hdr->abort_flag)) {
-                pick = -2;
-            } else if (globaltimer_ns() - sc.t_begin > KERNEL_LIMIT_FACTOR * L.timeout_ns) {
-                // whole-kernel limit: even a busy block cannot run unbounded
-                set_status(L.hdr, SSSP_ETIMEOUT);
-                atomicExch(&L.hdr->abort_flag, 1u);
-                pick = -2;
-            } else {
-                // Units in source order: a block serves its lower sources first, so
-                // the state in use at any time belongs to few sources (measured on
-                // R-MAT scale 22 with 8 sources: 8% faster than round-robin, in spite
-                // of more relaxations).
-                for (uint32_t j = 0; j < nu; ++j) {
-                    const uint32_t uid = blockIdx.x + j * gridDim.x;
-                    if (ld_relaxed(&L.dirty[uid]) != 0u && atomicExch(&L.dirty[uid], 0u) != 0u) {
-                        pick = (int)uid;
+            if (lane == 0) {
+                if (ld_relaxed(&L.hdr->abort_flag)) {
+                    pick = -2;
+                } else if (globaltimer_ns() - sc.t_begin > KERNEL_LIMIT_FACTOR * L.timeout_ns) {
+                    // whole-kernel limit: even a busy block cannot run unbounded
+                    set_status(L.hdr, SSSP_ETIMEOUT);
+                    atomicExch(&L.hdr->abort_flag, 1u);
+                    pick = -2;
+                }
+            }
+            pick = __shfl_sync(0xFFFFFFFFu, pick, 0);
+            for (uint32_t j0 = 0; pick == -1 && j0 < nu; j0 += 32u) {
+                const uint32_t uid = blockIdx.x + (j0 + lane) * gridDim.x;
+                uint32_t ball = __ballot_sync(0xFFFFFFFFu, j0 + lane < nu && ld_relaxed(&L.dirty[uid]) != 0u);
+                while (ball) {
+                    const uint32_t f = __ffs(ball) - 1u;
+                    uint32_t got = 0;
+                    if (lane == f) got = atomicExch(&L.dirty[uid], 0u);
+                    if (__shfl_sync(0xFFFFFFFFu, got, (int)f) != 0u) {
+                        pick = (int)(blockIdx.x + (j0 + f) * gridDim.x);
                         break;
                     }
+                    ball &= ball - 1u;
                 }
+            }
+            if (lane == 0) {
                 if (pick >= 0) {
-                    __threadfence();  // doorbell before the inbox scan
+                    // Reserve termination counts for the round before any of its inbox
+                    // bits can be visible (a round activates at most one vertex per
+                    // relaxed edge, fewer than ROUND_RESERVE); the same fence orders the
+                    // doorbell before the inbox scan.
+                    atomicAdd(&L.hdr->pending, ROUND_RESERVE);
+                    __threadfence();
                     if (sc.idle_start) sm.st[ST_IDLE] += globaltimer_ns() - sc.idle_start;
                     sc.idle_start = 0;
                     sc.backoff = 32;
-                } else if (ld_relaxed(&L.hdr->pending) == 0ull) {
+                } else if (pick == -1 && ld_relaxed(&L.hdr->pending) == 0ull) {
                     pick = -2;  // nothing queued, nothing in flight: terminated
                     if (sc.idle_start) sm.st[ST_IDLE] += globaltimer_ns() - sc.idle_start;
-                } else {
+                } else if (pick == -1) {
                     const uint64_t now = globaltimer_ns();
                     if (sc.idle_start == 0) {
                         sc.idle_start = now;
@@ -694,11 +695,11 @@ __global__ void __launch_bounds__(SOLVE_MAX_THREADS, 4) k_solve(SolveLaunch L) {
                     }
                     if (pick == -1) {
                         __nanosleep(sc.backoff);
-                        if (sc.backoff < 1024u) sc.backoff *= 2u;
+                        if (sc.backoff < IDLE_BACKOFF_MAX_NS) sc.backoff *= 2u;
                     }
                 }
+                sc.pick = pick;
             }
-            sc.pick = pick;
         }
         __syncthreads();
         const int pick = sc.pick;
@@ -711,7 +712,10 @@ __global__ void __launch_bounds__(SOLVE_MAX_THREADS, 4) k_solve(SolveLaunch L) {
         const uint32_t phi = min(plo + L.B, L.V);
         const uint32_t lo = plo + k * L.Bq;
         const uint32_t hi = min(lo + L.Bq, phi);
-        if (lo >= hi) continue;
+        if (lo >= hi) {  // an empty sub-block is never dirty; return the reservation all the same
+            if (threadIdx.x == 0) atomicAdd(&L.hdr->pending, 0ull - ROUND_RESERVE);
+            continue;
+        }
         c.packed = L.packed + (size_t)s * L.V;
         c.bitmap = L.bitmap + (size_t)s * L.words;
         c.dirty = L.dirty + (size_t)s * L.Q;
