@@ -233,6 +233,28 @@ sssp_status sssp_solve(const sssp_graph* g, const uint32_t* sources, uint32_t S,
                        const sssp_options* opt, void* ws, size_t ws_bytes, sssp_stream_t stream);
 
 /*
+ * Warm start (incremental SSSP; the paper has no such call): sssp_solve's result
+ * on a graph after some edge weights fell or edges were added, computed from the
+ * result before the change instead of from scratch.  Previous distances stay
+ * upper bounds when weights only fall, and relaxing the tails of the changed
+ * edges from them converges, as the label-correcting relaxation across
+ * partitions of Sec. III.C does from any upper bounds, to the same distances and
+ * canonical predecessors a fresh sssp_solve returns.
+ *   g          : the graph after the change (same vertex ids; may be a different CSR)
+ *   dist, pred : device [S][V] in/out: on entry a result of sssp_solve (or of this
+ *                call) for S sources on the graph before the change, in the caller's
+ *                ids; on exit the result on g.  pred must not be NULL.
+ *   tails      : device [n_tails] caller's ids of the tails of every edge whose weight
+ *                fell or that was added (repeats allowed); n_tails = 0 returns the input
+ *   opt, ws    : as for sssp_solve (ws >= sssp_solve_workspace_size(g, S, opt))
+ * A weight that rose is not allowed: the relaxation never raises a distance, so the
+ * result would keep the old, now too small, value.  Bad tail ids end with SSSP_EINVAL
+ * on the device status.
+ */
+sssp_status sssp_update(const sssp_graph* g, uint32_t S, void* dist, uint32_t* pred, const uint32_t* tails,
+                        uint32_t n_tails, const sssp_options* opt, void* ws, size_t ws_bytes, sssp_stream_t stream);
+
+/*
  * Autotuner for sssp_solve (the paper has no tuner; its knobs are the process
  * count and the termination timeout).  Runs sssp_solve on (g, sources) with
  * candidate schedules and returns the fastest: the bucket width delta is

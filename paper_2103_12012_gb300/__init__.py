@@ -72,6 +72,7 @@ _SIGS = {
     "sssp_solve_workspace_size": (sz, [P, u32, P]),
     "sssp_solve": (i32, [P, P, u32, P, P, P, P, sz, P]),
     "sssp_workspace_status": (i32, [P, P, P]),
+    "sssp_update": (i32, [P, u32, P, P, P, u32, P, P, sz, P]),
     "sssp_autotune": (i32, [P, P, u32, P, P, P, sz, P, u32, P, P, P]),
     "sssp_solve_noalloc": (i32, [P, P, u32, P, P, P, P, P]),
     "sssp_batch_workspace_size": (sz, [P, P]),
@@ -300,6 +301,17 @@ class Solver:
         _check(st, "sssp_solve")
         return dist, pred
 
+    def update(self, dist, pred, tails, stream=None):
+        """sssp_update (warm start), asynchronous: dist/pred hold a result for this solver's S
+        sources on the graph before some weights fell or edges were added; they are updated in
+        place to the result on this solver's graph.  tails: device int32 tensor of the changed
+        edges' tails (caller's ids)."""
+        n = 0 if tails is None else int(tails.numel())
+        st = lib().sssp_update(ctypes.byref(self.gc), self.S, _ptr(dist), _ptr(pred), _ptr(tails) if n else None, n,
+                               ctypes.byref(self.opts), _ptr(self.ws), self.ws_bytes, _stream(stream))
+        _check(st, "sssp_update")
+        return dist, pred
+
     def status(self, stream=None):
         stats = SsspStats()
         st = lib().sssp_workspace_status(_ptr(self.ws), _stream(stream), ctypes.byref(stats))
@@ -370,6 +382,20 @@ def solve(g: DeviceGraph, sources, opts: SsspOptions | None = None, check=True):
     s = Solver(g, len(sources) if not hasattr(sources, "numel") else sources.numel(), opts)
     d, p = s(sources, check=check)
     return d.clone(), p.clone(), s.last_status, s.last_stats
+
+
+def update(g: DeviceGraph, dist, pred, tails, opts: SsspOptions | None = None, check=True):
+    """Warm start: dist/pred ([S, V] tensors from a solve before some weights fell or edges were
+    added) updated in place to the result on g; tails = the changed edges' tails.  Returns
+    (dist, pred, status, stats)."""
+    s = Solver(g, int(dist.shape[0]), opts)
+    if isinstance(tails, np.ndarray) or isinstance(tails, (list, tuple)):
+        tails = _as_dev_u32(np.asarray(tails, np.uint32))
+    s.update(dist, pred, tails)
+    st, stats = s.status()
+    if check and st != SSSP_OK:
+        raise SsspError(st, "sssp_update (device)")
+    return dist, pred, st, stats
 
 
 class Batch:

@@ -174,10 +174,13 @@ size_t sssp_solve_workspace_size(const sssp_graph* g, uint32_t S, const sssp_opt
     return solve_layout(g, S, r.split).total;
 }
 
-sssp_status sssp_solve(const sssp_graph* g, const uint32_t* sources, uint32_t S, void* dist, uint32_t* pred,
-                       const sssp_options* opt, void* ws, size_t ws_bytes, sssp_stream_t stream) {
+// sssp_solve (sources given) and sssp_update (warm: from the result in dist/pred)
+static sssp_status solve_impl(const sssp_graph* g, const uint32_t* sources, uint32_t S, void* dist, uint32_t* pred,
+                              const sssp_options* opt, void* ws, size_t ws_bytes, sssp_stream_t stream,
+                              const uint32_t* tails, uint32_t n_tails, bool warm) {
     Resolved r;
-    if (!graph_ok(g) || S == 0 || !sources || !dist || !ws || !resolve(opt, g->wtype, &r)) return SSSP_EINVAL;
+    if (!graph_ok(g) || S == 0 || (!warm && !sources) || !dist || !ws || !resolve(opt, g->wtype, &r))
+        return SSSP_EINVAL;
     if (!aligned16(ws) || r.threads > SOLVE_MAX_THREADS) return SSSP_EINVAL;
     const SolveWs L = solve_layout(g, S, r.split);
     if ((uint64_t)S * L.Q > 0xFFFFFFFFull / 2 || L.Q > MAX_UNITS_PER_SOURCE * 16u) return SSSP_EINVAL;
@@ -219,7 +222,21 @@ sssp_status sssp_solve(const sssp_graph* g, const uint32_t* sources, uint32_t S,
     l.ev_end = r.ev_end;
     l.dist = static_cast<uint32_t*>(dist);
     l.pred = pred;
+    l.warm = warm ? 1u : 0u;
+    l.warm_tails = tails;
+    l.n_tails = n_tails;
     return launch_solve(l, (cudaStream_t)stream) == cudaSuccess ? SSSP_OK : SSSP_ECUDA;
+}
+
+sssp_status sssp_solve(const sssp_graph* g, const uint32_t* sources, uint32_t S, void* dist, uint32_t* pred,
+                       const sssp_options* opt, void* ws, size_t ws_bytes, sssp_stream_t stream) {
+    return solve_impl(g, sources, S, dist, pred, opt, ws, ws_bytes, stream, nullptr, 0, false);
+}
+
+sssp_status sssp_update(const sssp_graph* g, uint32_t S, void* dist, uint32_t* pred, const uint32_t* tails,
+                        uint32_t n_tails, const sssp_options* opt, void* ws, size_t ws_bytes, sssp_stream_t stream) {
+    if (!pred || (n_tails && !tails)) return SSSP_EINVAL;
+    return solve_impl(g, nullptr, S, dist, pred, opt, ws, ws_bytes, stream, tails, n_tails, true);
 }
 
 sssp_status sssp_autotune(const sssp_graph* g, const uint32_t* sources, uint32_t S, void* dist, uint32_t* pred,

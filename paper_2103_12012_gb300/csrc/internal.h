@@ -41,9 +41,13 @@ struct SolveLaunch {
     uint64_t timeout_ns;
     uint32_t hold_pending;
     cudaEvent_t ev_begin, ev_end;  // optional timing events around the relaxation kernel
-    // outputs
+    // outputs (and, for a warm start, the previous result they start from)
     uint32_t* dist;
     uint32_t* pred;
+    // warm start: tails of the edges whose weight fell or that were added
+    uint32_t warm;
+    const uint32_t* warm_tails;
+    uint32_t n_tails;
 };
 
 constexpr uint32_t SOLVE_MAX_THREADS = 512;  // block size limit of the solve kernel

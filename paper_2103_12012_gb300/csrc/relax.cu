@@ -586,6 +586,49 @@ __global__ void k_seed(SolveLaunch L) {
 
 // dist / pred in the caller's ids: element i of source s reads the packed word of
 // stored vertex slots[i] (predecessor labels are caller's ids already).
+// K0 (warm start): the packed words from a previous result, given in the caller's
+// order (dist [S][V], pred [S][V]); an unreached vertex gets the INF word.
+template <class W>
+__global__ void k_warm_pack(size_t n, uint32_t V, const uint32_t* __restrict__ slots,
+                            const uint32_t* __restrict__ dist, const uint32_t* __restrict__ pred,
+                            unsigned long long* __restrict__ packed) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const size_t s = i / V, j = i - s * V;
+        const size_t at = s * V + (slots ? __ldg(&slots[j]) : j);
+        const uint32_t d = dist[i];
+        packed[at] = d == W::inf_out() ? INF_KEY : ((unsigned long long)d << 32) | pred[i];
+    }
+}
+
+// K0 (warm start): queue, in every source, the tails of the edges whose weight fell or
+// that were added (a reached tail only: an unreached one relaxes nothing).  Relaxing
+// them from the previous distances, which stay upper bounds when weights only fall,
+// converges to the new result (label correcting, as the Bellman-Ford level of Sec. III.C).
+__global__ void k_warm_seed(SolveLaunch L) {
+    const size_t n = (size_t)L.S * L.n_tails;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    const size_t gtid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gtid == 0 && L.hold_pending) atomicAdd(&L.hdr->pending, 1ull);
+    for (size_t i = gtid; i < n; i += stride) {
+        const uint32_t s = (uint32_t)(i / L.n_tails);
+        const uint32_t t = L.warm_tails[i - (size_t)s * L.n_tails];
+        if (t >= L.V) {
+            set_status(L.hdr, SSSP_EINVAL);
+            continue;
+        }
+        const uint32_t v = L.slots ? L.slots[t] : t;
+        if (L.packed[(size_t)s * L.V + v] == INF_KEY) continue;
+        const uint32_t bit = 1u << (v & 31u);
+        if (atomicOr(&L.bitmap[(size_t)s * L.words + (v >> 5)], bit) & bit) continue;  // listed twice
+        const uint32_t p = v / L.B;
+        const uint32_t q = p * L.split + (v - p * L.B) / L.Bq;
+        atomicAdd(&L.hdr->pending, 1ull);
+        __threadfence();
+        L.dirty[(size_t)s * L.Q + q] = 1u;
+    }
+}
+
 template <class W>
 __global__ void k_unpack(const unsigned long long* __restrict__ packed, size_t n, uint32_t V,
                          const uint32_t* __restrict__ slots, uint32_t* __restrict__ dist, uint32_t* __restrict__ pred) {
@@ -837,9 +880,22 @@ cudaError_t launch_solve(const SolveLaunch& L, cudaStream_t st) {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const size_t want = (n_packed / 2 + 255) / 256;
         const unsigned blocks = (unsigned)std::min<size_t>(std::max<size_t>(want, 1), (size_t)sms * 8);
-        k_init_fill<<<blocks, 256, 0, st>>>(L.packed, n_packed, L.bitmap, n_words, L.dirty, n_dirty);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        k_seed<<<(L.S + 127) / 128, 128, 0, st>>>(L);
+        if (L.warm) {
+            if ((e = cudaMemsetAsync(L.bitmap, 0, 4 * n_words, st)) != cudaSuccess) return e;
+            if ((e = cudaMemsetAsync(L.dirty, 0, 4 * n_dirty, st)) != cudaSuccess) return e;
+            if (L.wtype == SSSP_W_F32)
+                k_warm_pack<WF32><<<blocks, 256, 0, st>>>(n_packed, L.V, L.slots, L.dist, L.pred, L.packed);
+            else
+                k_warm_pack<WU32><<<blocks, 256, 0, st>>>(n_packed, L.V, L.slots, L.dist, L.pred, L.packed);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            const size_t nt = (size_t)L.S * L.n_tails;
+            const unsigned tb = (unsigned)std::min<size_t>(std::max<size_t>((nt + 255) / 256, 1), (size_t)sms * 8);
+            k_warm_seed<<<tb, 256, 0, st>>>(L);
+        } else {
+            k_init_fill<<<blocks, 256, 0, st>>>(L.packed, n_packed, L.bitmap, n_words, L.dirty, n_dirty);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            k_seed<<<(L.S + 127) / 128, 128, 0, st>>>(L);
+        }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     const size_t smem = relax_smem_bytes(L.tile, L.Q);

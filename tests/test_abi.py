@@ -114,3 +114,15 @@ def test_layout_host_checks_without_gpu(L):
     assert L.sssp_layout(ctypes.byref(lay), 16, 16, 16, None, 16, 16, 16, need, None) == sssp.SSSP_EINVAL
     # the tree backward indexes edges of the graph it is given: a layout graph is refused
     assert L.sssp_backward(ctypes.byref(lay), 1, 16, 16, 16, 16, 1 << 30, None) == sssp.SSSP_EINVAL
+
+
+def test_update_host_checks_without_gpu(L):
+    g = _graph(V=1000, E=5000, P=4)
+    # pred is required (the previous predecessors seed the canonical ones); tails unless n_tails = 0
+    assert L.sssp_update(ctypes.byref(g), 1, 16, None, 16, 1, None, 16, 1 << 30, None) == sssp.SSSP_EINVAL
+    assert L.sssp_update(ctypes.byref(g), 1, 16, 16, None, 3, None, 16, 1 << 30, None) == sssp.SSSP_EINVAL
+    assert L.sssp_update(ctypes.byref(g), 0, 16, 16, 16, 1, None, 16, 1 << 30, None) == sssp.SSSP_EINVAL
+    assert L.sssp_update(None, 1, 16, 16, 16, 1, None, 16, 1 << 30, None) == sssp.SSSP_EINVAL
+    need = L.sssp_solve_workspace_size(ctypes.byref(g), 2, None)
+    assert L.sssp_update(ctypes.byref(g), 2, 16, 16, 16, 1, None, 16, need - 1, None) == sssp.SSSP_ENOMEM
+

@@ -210,6 +210,69 @@ def test_solve_schedule_does_not_change_result(sssp, opts):
     check_solve(sssp, g, ref, [3, 19999, 12345], sssp.options(**opts))
 
 
+def _lowered(seed, src, dst, w, V, frac=0.02, add=0.01, f32=False):
+    """The edge list after some weights fell and some edges were added; returns it and the
+    tails of the changed edges."""
+    rng = np.random.default_rng(seed)
+    E = len(src)
+    pick = rng.random(E) < frac
+    w2 = w.copy()
+    if f32:
+        w2[pick] = (w2[pick] * rng.uniform(0.3, 1.0, int(pick.sum()))).astype(np.float32)
+    else:
+        w2[pick] = np.maximum(1, w2[pick] // rng.integers(1, 4, int(pick.sum()))).astype(np.uint32)
+    na = int(add * E)
+    s_add = rng.integers(0, V, na).astype(np.uint32)
+    d_add = rng.integers(0, V, na).astype(np.uint32)
+    w_add = (rng.uniform(0.5, 2.0, na).astype(np.float32) if f32 else rng.integers(1, 256, na).astype(np.uint32))
+    tails = np.concatenate([src[pick], s_add]).astype(np.uint32)
+    return (np.concatenate([src, s_add]), np.concatenate([dst, d_add]), np.concatenate([w2, w_add]), tails)
+
+
+@pytest.mark.parametrize("seed,V,E,P,f32,lay", [(70, 20000, 200000, 148, False, False), (71, 20000, 200000, 37, False, True),
+                                                (72, 5000, 40000, 5, True, False), (73, 3000, 9000, 3, False, False)])
+def test_update_warm_start_equals_fresh_solve(sssp, seed, V, E, P, f32, lay):
+    src, dst, w = raw_graph(seed, V, E, f32=f32, whi=60)
+    g = sssp.build_csr(V, src, dst, w, partitions=P)
+    if lay:
+        g = sssp.layout(g)
+    sources = np.array([0, 11, V - 1], np.uint32)
+    dist, pred, st, _ = sssp.solve(g, sources)
+    assert st == sssp.SSSP_OK
+    src2, dst2, w2, tails = _lowered(seed + 1, src, dst, w, V, f32=f32)
+    ref2 = oracle.csr(V, src2, dst2, w2)
+    g2 = sssp.build_csr(V, src2, dst2, w2, partitions=P)
+    if lay:
+        g2 = sssp.layout(g2)
+    dist, pred, st, stats = sssp.update(g2, dist, pred, tails)
+    assert st == sssp.SSSP_OK
+    for i, s in enumerate(sources):
+        d, p, _ = oracle.dijkstra(ref2, int(s))
+        assert np.array_equal(u32(dist[i]), d.view(np.uint32)), f"dist mismatch, source {s}"
+        assert np.array_equal(u32(pred[i]), p), f"pred mismatch, source {s}"
+    # far less work than a fresh solve on the changed graph
+    _, _, _, fresh = sssp.solve(g2, sources)
+    assert stats["edges_scanned"] < fresh["edges_scanned"]
+
+
+def test_update_with_nothing_changed_and_unreached_tails(sssp):
+    V = 4000
+    src, dst, w = raw_graph(74, V, 6000)
+    g = sssp.build_csr(V, src, dst, w, partitions=4)
+    sources = np.array([5], np.uint32)
+    dist, pred, _, _ = sssp.solve(g, sources)
+    d0, p0 = dist.clone(), pred.clone()
+    sssp.update(g, dist, pred, np.zeros(0, np.uint32))
+    assert torch.equal(dist, d0) and torch.equal(pred, p0)
+    unreached = np.flatnonzero(u32(d0[0]) == 0xFFFFFFFF).astype(np.uint32)[:50]
+    assert len(unreached) > 0
+    dist, pred, st, stats = sssp.update(g, dist, pred, np.concatenate([unreached, unreached]))
+    assert st == sssp.SSSP_OK and torch.equal(dist, d0) and torch.equal(pred, p0)
+    assert stats["edges_scanned"] == 0
+    with pytest.raises(sssp.SsspError):
+        sssp.update(g, dist, pred, np.array([V + 3], np.uint32))
+
+
 def test_solve_f32_bit_exact(sssp):
     g0 = gg.rmat(gg.BASE_SEED + 50, 14, 8 << 14, wf32=(0.5, 2.0, 1e-4))
     ref = oracle.csr_of(g0)
