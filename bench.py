@@ -523,9 +523,53 @@ def extras_grid(sssp, dev):
             "work_inflation": round(stats["edges_scanned"] / g.E, 3)}
 
 
+def extras_warm(sssp, dev):
+    """R-MAT scale 22, 8 sources, locality layout: 0.1% of the weights halved; sssp_update from the
+    previous result against a fresh solve of the changed graph (results must be equal)."""
+    import torch
+    g0, srcs, P = gg.workload_rmat22()
+    g = sssp.layout(sssp.build_csr(g0.V, g0.src, g0.dst, g0.w, partitions=P))
+    del g0
+    src_d = torch.from_numpy(srcs.view(np.int32)).to(dev)
+    opts, _ = sssp.autotune(g, src_d)
+    rng = np.random.default_rng(gg.BASE_SEED + 40)
+    idx = torch.from_numpy(np.sort(rng.choice(g.E, g.E // 1000, replace=False)).astype(np.int64)).to(dev)
+    w2 = g.w.clone()
+    w2[idx] = torch.clamp(w2[idx] // 2, min=1)
+    tails = g.ids.long()[torch.searchsorted(g.row_ptr.long(), idx, right=True) - 1].int()  # caller's ids
+    g2 = sssp.DeviceGraph(g.V, g.E, g.row_ptr, g.col, w2, g.wtype, g.partitions, g.eid, g.ids, g.slots)
+    s1, s2 = sssp.Solver(g, len(srcs), opts), sssp.Solver(g2, len(srcs), opts)
+    s1.launch(src_d)
+    d0, p0 = s1.dist.clone(), s1.pred.clone()
+    s2.launch(src_d)
+    st, fresh = s2.status()
+    assert st == sssp.SSSP_OK
+    fresh_ms = _time_ms(lambda: s2.launch(src_d), 3)
+    d, p = d0.clone(), p0.clone()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    times = []
+    for _ in range(4):
+        d.copy_(d0)
+        p.copy_(p0)
+        e0.record()
+        s2.update(d, p, tails)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    st, warm = s2.status()
+    assert st == sssp.SSSP_OK
+    equal = bool(torch.equal(d, s2.dist) and torch.equal(p, s2.pred))
+    upd_ms = statistics.median(times[1:])
+    return {"workload": "rmat-s22-ef16, 8 sources, layout; 0.1% of the weights halved", "changed_edges": int(idx.numel()),
+            "fresh_solve_ms": round(fresh_ms, 3), "update_ms": round(upd_ms, 3),
+            "speedup": round(fresh_ms / upd_ms, 2), "update_edges_scanned": warm["edges_scanned"],
+            "fresh_edges_scanned": fresh["edges_scanned"], "equal_to_fresh": equal}
+
+
 def extras(sssp, dev):
     out = {}
-    for name, fn in (("batched", extras_batched), ("differentiable", extras_differentiable), ("grid", extras_grid)):
+    for name, fn in (("batched", extras_batched), ("differentiable", extras_differentiable), ("grid", extras_grid),
+                     ("warm_start", extras_warm)):
         t0 = time.perf_counter()
         try:
             out[name] = fn(sssp, dev)
