@@ -76,16 +76,26 @@ def rank_sources(g, rank, count=8):
     return gg.pick_sources(seed, g, count)
 
 
+def code_sha256(path):
+    """sha256 of a CUDA source with its comments and blank lines removed: what the capture of a
+    kernel depends on (a comment edit keeps the capture valid, a code edit does not)."""
+    import hashlib
+    import re
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    lines = [re.sub(r"//.*$", "", ln).rstrip() for ln in text.splitlines()]
+    return hashlib.sha256("\n".join(ln for ln in lines if ln.strip()).encode()).hexdigest()
+
+
 def dram_traffic(edges_scanned):
     """DRAM bytes per launch of the relaxation kernel from the committed ncu capture, scaled to this
-    launch by edges scanned; None if the kernel source changed since that capture."""
-    import hashlib
+    launch by edges scanned; None if the kernel code changed since that capture."""
     try:
         rec = json.loads(open(os.path.join(ROOT, "profiles", "k_solve_dram_traffic.txt")).read())
-        src = open(os.path.join(ROOT, rec["source"]), "rb").read()
+        sha = code_sha256(os.path.join(ROOT, rec["source"]))
     except (OSError, ValueError, KeyError):
         return None, "no capture"
-    if hashlib.sha256(src).hexdigest() != rec["source_sha256"]:
+    if sha != rec["code_sha256"]:
         return None, "kernel changed since the capture"
     return int(rec["dram_bytes_per_scanned_edge"] * edges_scanned), rec["capture"] + ", scaled by edges scanned"
 

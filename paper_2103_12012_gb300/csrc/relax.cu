@@ -1,39 +1,46 @@
-// K0 init / K4 persistent relaxation / K5 batched relaxation / unpack.
+// K0 init (fresh or warm) / K4 persistent relaxation / K5 batched relaxation / unpack.
 //
 // The SP-Async loop of Sec. III.C on one GPU.  Vertices are split into
 // units: a unit is one sub-block of one partition (Sec. III.A 1D block
 // partitioning, sub-divided `split` ways) for one source.  Each unit has one
-// owner thread block.  Per source the device state is
-//   packed[v] : 64-bit word (dist << 32 | pred), lowered only by atomicMin;
+// owner thread block (unit b, b + grid, ...), which serves its dirty units in
+// source order.  Per source the device state is
+//   packed[v] : 64-bit word (dist << 32 | label), lowered only by atomicMin;
 //               dist is the uint32 distance or the bits of a non-negative
-//               float32 distance, whose unsigned order is the numeric order.
+//               float32 distance, whose unsigned order is the numeric order;
+//               label is the predecessor's id in the caller's numbering.
 //   bitmap[v] : 1 bit per vertex, the inbox: set when v's distance dropped
 //               and v must be (re)processed (Alg. 2 pq.push / Alg. 3 push or
 //               send_msg), cleared by the owner when it takes v.
 //   dirty[q]  : a unit's doorbell, rung after new bits land in its range.
 // A round of a unit (Alg. 2 recv_msgs + DIJKSTRA, bucketed):
-//   A  scan the unit's inbox words, read each queued vertex's distance, and
-//      find the minimum dmin;
-//   B  select the queued vertices with dist < dmin + delta (the near bucket,
+//   A  enumerate the unit's queued vertices (warp-cooperative over the inbox
+//      words), read their distances, find the minimum dmin, and keep those
+//      below (running minimum + delta), a superset of the bucket;
+//   B  select from them the ones with dist < dmin + delta (the near bucket,
 //      an approximation of Dijkstra's pop order inside the partition), at
 //      most `tile` of them;
 //   C  take them: clear their inbox bits (acquire);
 //   D  re-read their distances and CSR row extents; prefix-sum the degrees;
-//   E  relax every out-edge of the taken vertices with the whole block in
-//      edge-parallel, coalesced order: cand = d(u)+w(u,v); if the packed key
-//      (cand, u) is below the target's word, atomicMin it; if that lowered
-//      the distance, set v's inbox bit (release) -- a local push when v is
-//      in this unit, a message (Alg. 3 send_msg) otherwise;
+//   E  relax every out-edge of the taken vertices with the whole block:
+//      cand = d(u)+w(u,v); if it beats the target's distance (read first),
+//      atomicMin the packed word with (cand, label(u)); if that lowered the
+//      distance, set v's inbox bit after a release fence -- a message (Alg. 3
+//      send_msg) when v is in another unit; a vertex of this unit that falls
+//      below the bucket bound goes to a shared-memory queue instead and is
+//      relaxed by a sub-round of the same round (Dijkstra inside the unit);
 //   F  settle the termination count and ring the doorbells of every unit
-//      that received a new vertex.
+//      that received a new vertex (and this unit's own if vertices are left).
 // Termination (Sec. III.D, the message counter of ToKa): `pending` counts
-// queued vertices plus vertices taken but not yet finished.  A round first
-// reserves one count per edge it will relax (so a vertex is counted before
-// its bit is visible), then returns the unused reservations and its taken
-// vertices.  pending == 0 therefore means no queued and no in-flight work
-// anywhere, and it can never rise again; every block then exits.  Every wait
-// is bounded by a %globaltimer limit after which the block records
-// SSSP_ETIMEOUT, raises the abort flag and returns.
+// queued vertices plus the reservations of rounds in flight.  A block takes a
+// fixed reservation (more than a round can activate) when it picks a unit,
+// before any of the round's bits can be visible, and returns it at the end of
+// the round together with the vertices it took, adding the ones it activated.
+// pending == 0 therefore means no queued and no in-flight work anywhere, and
+// it can never rise again; every block then exits.  Every wait is bounded by a
+// %globaltimer limit after which the block records SSSP_ETIMEOUT, raises the
+// abort flag and returns.  A warm start packs a previous result instead of
+// the INF words and queues the tails of the changed edges.
 #include <algorithm>
 
 #include "common.cuh"
