@@ -410,7 +410,7 @@ BatchWs batch_layout(uint32_t n_problems, uint64_t total_out, uint64_t total_wor
     w.off_packed = off;
     off += align_up(8ull * total_out, 256);
     w.off_bitmap = off;
-    off += align_up(4ull * total_words, 256);
+    off += align_up(4ull * total_words * batched_bitmaps(), 256);
     w.total = off;
     return w;
 }

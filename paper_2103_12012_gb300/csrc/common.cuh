@@ -70,6 +70,8 @@ struct WU32 {
     }
     __device__ __forceinline__ static bool weight_ok(uint32_t w) { return w >= 1u; }
     __device__ __forceinline__ static uint32_t inf_out() { return INF32; }
+    // index of the width-delta distance bucket of d (delta >= 1); non-decreasing in d
+    __device__ __forceinline__ static uint32_t bucket(uint32_t d, uint32_t delta) { return d / delta; }
 };
 
 struct WF32 {
@@ -82,6 +84,12 @@ struct WF32 {
     // positive, finite, not NaN
     __device__ __forceinline__ static bool weight_ok(uint32_t w) { return w > 0u && w < F32_INF_BITS; }
     __device__ __forceinline__ static uint32_t inf_out() { return F32_INF_BITS; }
+    // index of the width-delta distance bucket of d: the rounded quotient, truncated (rounding
+    // and truncation are both monotone, so the index is non-decreasing in d)
+    __device__ __forceinline__ static uint32_t bucket(uint32_t d, uint32_t delta_bits) {
+        const float q = __fdiv_rn(__uint_as_float(d), __uint_as_float(delta_bits));
+        return q < 4.0e9f ? (uint32_t)q : 4000000000u;
+    }
 };
 
 }  // namespace sssp

@@ -80,6 +80,7 @@ struct BatchLaunch {
     cudaEvent_t ev_begin, ev_end;
 };
 
+uint32_t batched_bitmaps();  // inbox bitmaps per batched problem (distance buckets + overflow)
 cudaError_t batched_max_blocks_per_sm(int wtype, uint32_t threads, uint32_t tile, int* out);
 cudaError_t launch_batched(const BatchLaunch& L, cudaStream_t st);
 

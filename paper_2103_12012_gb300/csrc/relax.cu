@@ -55,6 +55,9 @@ constexpr uint32_t MAX_SUBROUNDS = 256;       // local sub-rounds one round may 
 constexpr uint32_t GATHER_MIN = 1024;          // queued vertices one scan can keep (at least)
 constexpr int GATHER_G = 2;                   // queued vertices a lane enumerates and loads together
 constexpr uint32_t IDLE_BACKOFF_MAX_NS = 1024;  // longest sleep of a block with no dirty unit
+// batched distance buckets: BK_NB fine buckets of width delta (the current coarse bucket),
+// BK_NC coarse buckets of width BK_NB * delta after it, then one overflow
+constexpr uint32_t BK_NB = 16, BK_NC = 16, BK_OV = BK_NB + BK_NC, BK_SLOTS = BK_NB + BK_NC + 1;
 constexpr int EDGE_BATCH = 3;                // edges in flight per thread in phase E (measured: 2-4 similar)
 constexpr unsigned long long ROUND_RESERVE = 1ull << 32;  // termination counts reserved per round (> edges)
 
@@ -178,6 +181,10 @@ __device__ __forceinline__ uint32_t bucket_bound(uint32_t dmin, uint32_t delta) 
 
 struct Scalars {
     uint32_t cnt, nlist, dmin, nsel, nclaim, act, bad, nlq;
+    // batched buckets: current coarse bucket (absolute), current fine slot, least coarse
+    // bucket in the overflow (a lower bound), this round's operation and slot, and the set
+    // bits of each slot (fine, coarse, overflow)
+    uint32_t bk_k0, bk_f, bk_ovmin, bk_op, bk_slot, bk_cnt[BK_SLOTS];
     int pick;
     unsigned long long prob;
     // thread 0's scheduling state (static mode), here rather than in every thread's registers
@@ -203,6 +210,7 @@ struct Ctx {
     // static-ownership mode only
     uint32_t* dirty;  // this source's unit doorbells
     uint32_t B, Bq, split, Qw;
+    uint32_t words;  // batched buckets: inbox words of one bucket bitmap
 };
 
 struct Smem {
@@ -219,9 +227,10 @@ struct Smem {
 
 // One round over the unit owning vertices [lo, hi).  Returns the number of
 // queued vertices the scan found (0 = the unit's inbox was empty).
-template <class W, bool STATIC>
+template <class W, bool STATIC, bool BK>
 __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t my_q,
                                 const Smem& sm) {
+    static_assert(!(STATIC && BK), "distance buckets belong to the batched kernel");
     const uint32_t T = blockDim.x, tid = threadIdx.x, lane = tid & 31u;
     Scalars& sc = *sm.sc;
     if (tid == 0) {
@@ -236,107 +245,272 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
     }
     __syncthreads();
 
-    // ---- A: scan the inbox: count the queued vertices, find their minimum distance
-    // and keep the candidates for the near bucket.  Each warp takes 32 words; its
-    // lanes enumerate the set bits by rank, GATHER_G each with their distance loads
-    // in flight together.  The block minimum only falls as the scan goes on, so a
-    // vertex at or above (running minimum + delta) can never enter the bucket: only
-    // the ones below it are kept (a superset of the bucket, usually far smaller
-    // than all queued vertices).
-    const uint32_t wlo = lo >> 5, whi = (hi - 1u) >> 5;
-    for (uint32_t wb = wlo + (tid & ~31u); wb <= whi; wb += T) {
-        const uint32_t wd = wb + lane;
-        const uint32_t bits = wd <= whi ? ld_relaxed(&c.bitmap[wd]) & range_mask(wd, lo, hi) : 0u;
-        const uint32_t incl = warp_scan_incl((uint32_t)__popc(bits), lane);
-        const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-        if (total == 0) continue;
-        if (lane == 0) atomicAdd(&sc.cnt, total);
-        for (uint32_t i0 = lane; i0 < total + lane; i0 += 32u * GATHER_G) {  // warp-uniform trip count
-            uint32_t vs[GATHER_G], ds[GATHER_G];
-#pragma unroll
-            for (int g = 0; g < GATHER_G; ++g)
-                vs[g] = nth_queued(wb, bits, incl, min(i0 + 32u * g, total - 1u));
-            uint32_t bm = 0xFFFFFFFFu;
-#pragma unroll
-            for (int g = 0; g < GATHER_G; ++g) {
-                ds[g] = i0 + 32u * g < total ? (uint32_t)(__ldcg(&c.packed[vs[g]]) >> 32) : 0xFFFFFFFFu;
-                bm = min(bm, ds[g]);
+    uint32_t found = 0, nsel = 0, te = 0, thr = 0, bkb = 0;
+    if constexpr (BK) {
+        // ---- Distance buckets (batched: one block owns the whole problem, so every
+        // producer is this block), a two-level radix structure: a vertex is queued in the
+        // fine bucket (width delta) of its distance when that lies in the current coarse
+        // bucket k0, else in coarse bucket k0+1 .. k0+BK_NC (width BK_NB * delta), else in
+        // the overflow.  A round relaxes the lowest non-empty fine bucket; an exhausted
+        // coarse bucket is split into the fine ones, the overflow moved in when its least
+        // coarse bucket comes within reach.  So a queued vertex is read a few times in all
+        // instead of once per round.  Relaxing fine bucket b only yields distances in
+        // bucket b or later, so an entry whose vertex's distance has fallen into a finished
+        // bucket is stale (the vertex was relaxed there) and is dropped.
+        enum { OP_DONE, OP_PROCESS, OP_SPLIT, OP_FLUSH, OP_FLUSH_NEW };
+        if (tid == 0) {
+            uint32_t op = OP_DONE, slot = NONE;
+            const uint32_t k0 = sc.bk_k0;
+            if (sc.bk_cnt[BK_OV] && sc.bk_ovmin <= k0 + BK_NC) {
+                op = OP_FLUSH;  // overflow entries that belong in the coarse window move in first
+            } else {
+                for (uint32_t f = sc.bk_f; f < BK_NB; ++f)
+                    if (sc.bk_cnt[f]) {
+                        op = OP_PROCESS;
+                        slot = f;
+                        sc.bk_f = f;
+                        break;
+                    }
+                if (op == OP_DONE) {
+                    for (uint32_t j = 1; j <= BK_NC; ++j)
+                        if (sc.bk_cnt[BK_NB + (k0 + j) % BK_NC]) {
+                            op = OP_SPLIT;
+                            slot = k0 + j;  // the coarse bucket to split
+                            break;
+                        }
+                }
+                if (op == OP_DONE && sc.bk_cnt[BK_OV]) op = OP_FLUSH_NEW;
             }
-            bm = warp_min(bm);  // lane 0's first element is valid: bm is a distance
-            if (lane == 0) atomicMin(&sc.dmin, bm);
-            const uint32_t bound = bucket_bound<W>(min(bm, *(volatile uint32_t*)&sc.dmin), c.delta);
+            sc.bk_op = op;
+            sc.bk_slot = slot;
+        }
+        __syncthreads();
+        const uint32_t op = sc.bk_op, k0 = sc.bk_k0;
+        uint32_t* const bmap = c.bitmap;
+        auto slot_bm = [&](uint32_t sl) { return bmap + (size_t)sl * c.words; };
+        auto for_each_set = [&](const uint32_t* bm, auto&& f) {  // warp-uniform calls f(ok, v)
+            for (uint32_t wb = tid & ~31u; wb < c.words; wb += T) {
+                const uint32_t wd = wb + lane;
+                const uint32_t bits = wd < c.words ? __ldcg(&bm[wd]) : 0u;
+                const uint32_t incl = warp_scan_incl((uint32_t)__popc(bits), lane);
+                const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+                for (uint32_t i0 = lane; i0 < total + lane; i0 += 32u)
+                    f(i0 < total, nth_queued(wb, bits, incl, min(i0, total - 1u)));
+            }
+        };
+        auto dist = [&](uint32_t v) { return (uint32_t)(__ldcg(&c.packed[v]) >> 32); };
+        // move v (its bit set in slot `from`) to the slot of fine bucket b under current coarse
+        // bucket `base`; false if it belongs where it is
+        auto move = [&](uint32_t* from_bm, uint32_t from, uint32_t v, uint32_t b, uint32_t base) {
+            const uint32_t kc = b / BK_NB;
+            const uint32_t to = kc == base ? b % BK_NB : kc <= base + BK_NC ? BK_NB + kc % BK_NC : BK_OV;
+            if (to == from) return false;
+            const uint32_t bit = 1u << (v & 31u);
+            atomicAnd(&from_bm[v >> 5], ~bit);
+            if (!(atomicOr(&slot_bm(to)[v >> 5], bit) & bit)) atomicAdd(&sc.bk_cnt[to], 1u);
+            if (to == BK_OV) atomicMin(&sc.bk_ovmin, kc);
+            return true;
+        };
+        if (op == OP_PROCESS) {
+            // take up to `tile` queued vertices of the fine bucket (A/B), then (C/D) claim them,
+            // drop the stale ones, read distances and row extents
+            found = 1;
+            const uint32_t slot = sc.bk_slot;
+            bkb = k0 * BK_NB + slot;
+            uint32_t* const bm = slot_bm(slot);
+            for_each_set(bm, [&](bool ok, uint32_t v) {
+                const uint32_t k = warp_slot(ok, &sc.nsel, lane);
+                if (k < c.tile) sm.sel_v[k] = v;
+            });
+            __syncthreads();
+            nsel = min(sc.nsel, c.tile);
+            uint32_t myproc = 0;
+            for (uint32_t i = tid; i < nsel; i += T) {
+                const uint32_t u = sm.sel_v[i];
+                atomicAnd(&bm[u >> 5], ~(1u << (u & 31u)));
+                const uint32_t du = dist(u);
+                uint32_t deg = 0, beg = 0;
+                if (W::bucket(du, c.delta) < bkb) {
+                    sm.sel_v[i] = NONE;
+                } else {
+                    ++myproc;
+                    beg = __ldg(&c.row_ptr[u]);
+                    deg = __ldg(&c.row_ptr[u + 1]) - beg;
+                }
+                sm.list_d[i] = du;
+                sm.list_v[i] = beg;
+                sm.sel_pref[i] = deg;
+            }
+            myproc = warp_sum(myproc);
+            if (lane == 0 && myproc) atomicAdd(&sc.nclaim, myproc);
+            if (tid == 0) sc.bk_cnt[slot] -= nsel;
+        } else if (op == OP_SPLIT) {
+            // the fine buckets are exhausted: the next non-empty coarse bucket becomes k0 and
+            // is split into them (entries whose distance fell into a finished bucket leave)
+            found = 1;
+            const uint32_t kn = sc.bk_slot, from = BK_NB + kn % BK_NC;
+            uint32_t* const bm = slot_bm(from);
+            uint32_t gone = 0;
+            for_each_set(bm, [&](bool ok, uint32_t v) {
+                if (!ok) return;
+                const uint32_t b = W::bucket(dist(v), c.delta);
+                ++gone;
+                if (b / BK_NB < kn)  // stale
+                    atomicAnd(&bm[v >> 5], ~(1u << (v & 31u)));
+                else
+                    move(bm, from, v, b, kn);
+            });
+            gone = warp_sum(gone);
+            if (lane == 0 && gone) atomicSub(&sc.bk_cnt[from], gone);
+            __syncthreads();
+            if (tid == 0) {
+                sc.bk_k0 = kn;
+                sc.bk_f = 0;
+            }
+        } else if (op == OP_FLUSH || op == OP_FLUSH_NEW) {
+            // move the overflow into the window; for OP_FLUSH_NEW (nothing else queued) the
+            // new current coarse bucket is the least live one of the overflow
+            found = 1;
+            uint32_t* const ov = slot_bm(BK_OV);
+            uint32_t base = k0;
+            if (op == OP_FLUSH_NEW) {
+                for_each_set(ov, [&](bool ok, uint32_t v) {
+                    uint32_t d = ok ? dist(v) : 0xFFFFFFFFu;
+                    if (ok && W::bucket(d, c.delta) / BK_NB <= k0) d = 0xFFFFFFFFu;  // stale
+                    const uint32_t m = warp_min(d);
+                    if (lane == 0 && m != 0xFFFFFFFFu) atomicMin(&sc.dmin, m);
+                });
+                __syncthreads();
+                if (sc.dmin != 0xFFFFFFFFu) base = W::bucket(sc.dmin, c.delta) / BK_NB;
+            }
+            if (tid == 0) sc.bk_ovmin = 0xFFFFFFFFu;
+            __syncthreads();
+            uint32_t gone = 0;
+            for_each_set(ov, [&](bool ok, uint32_t v) {
+                if (!ok) return;
+                const uint32_t b = W::bucket(dist(v), c.delta);
+                const uint32_t kc = b / BK_NB;
+                if (kc <= k0) {  // stale: fallen into a finished coarse bucket
+                    atomicAnd(&ov[v >> 5], ~(1u << (v & 31u)));
+                    ++gone;
+                } else if (move(ov, BK_OV, v, b, base)) {
+                    ++gone;
+                } else {
+                    atomicMin(&sc.bk_ovmin, kc);  // stays in the overflow
+                }
+            });
+            gone = warp_sum(gone);
+            if (lane == 0 && gone) atomicSub(&sc.bk_cnt[BK_OV], gone);
+            __syncthreads();
+            if (tid == 0 && op == OP_FLUSH_NEW) {
+                sc.bk_k0 = base;
+                sc.bk_f = 0;
+            }
+        }
+    } else {
+        // ---- A: scan the inbox: count the queued vertices, find their minimum distance
+        // and keep the candidates for the near bucket.  Each warp takes 32 words; its
+        // lanes enumerate the set bits by rank, GATHER_G each with their distance loads
+        // in flight together.  The block minimum only falls as the scan goes on, so a
+        // vertex at or above (running minimum + delta) can never enter the bucket: only
+        // the ones below it are kept (a superset of the bucket, usually far smaller
+        // than all queued vertices).
+        const uint32_t wlo = lo >> 5, whi = (hi - 1u) >> 5;
+        for (uint32_t wb = wlo + (tid & ~31u); wb <= whi; wb += T) {
+            const uint32_t wd = wb + lane;
+            const uint32_t bits = wd <= whi ? ld_relaxed(&c.bitmap[wd]) & range_mask(wd, lo, hi) : 0u;
+            const uint32_t incl = warp_scan_incl((uint32_t)__popc(bits), lane);
+            const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+            if (total == 0) continue;
+            if (lane == 0) atomicAdd(&sc.cnt, total);
+            for (uint32_t i0 = lane; i0 < total + lane; i0 += 32u * GATHER_G) {  // warp-uniform trip count
+                uint32_t vs[GATHER_G], ds[GATHER_G];
 #pragma unroll
-            for (int g = 0; g < GATHER_G; ++g) {
-                const uint32_t k = warp_slot(ds[g] < bound, &sc.nlist, lane);
-                if (k < c.gcap) {
-                    sm.list_v[k] = vs[g];
-                    sm.list_d[k] = ds[g];
+                for (int g = 0; g < GATHER_G; ++g)
+                    vs[g] = nth_queued(wb, bits, incl, min(i0 + 32u * g, total - 1u));
+                uint32_t bm = 0xFFFFFFFFu;
+#pragma unroll
+                for (int g = 0; g < GATHER_G; ++g) {
+                    ds[g] = i0 + 32u * g < total ? (uint32_t)(__ldcg(&c.packed[vs[g]]) >> 32) : 0xFFFFFFFFu;
+                    bm = min(bm, ds[g]);
+                }
+                bm = warp_min(bm);  // lane 0's first element is valid: bm is a distance
+                if (lane == 0) atomicMin(&sc.dmin, bm);
+                const uint32_t bound = bucket_bound<W>(min(bm, *(volatile uint32_t*)&sc.dmin), c.delta);
+#pragma unroll
+                for (int g = 0; g < GATHER_G; ++g) {
+                    const uint32_t k = warp_slot(ds[g] < bound, &sc.nlist, lane);
+                    if (k < c.gcap) {
+                        sm.list_v[k] = vs[g];
+                        sm.list_d[k] = ds[g];
+                    }
                 }
             }
+        }
+        __syncthreads();
+        found = sc.cnt;
+        if (found != 0) {
+            thr = bucket_bound<W>(sc.dmin, c.delta);
+            const uint32_t nkept = sc.nlist;
+
+            // ---- B: the near bucket, at most `tile` vertices: from the kept candidates,
+            // or, when there were more of them than the list holds, by enumerating the
+            // inbox again
+            if (nkept <= c.gcap) {
+                for (uint32_t i = tid; i < nkept + lane; i += T) {  // warp-uniform trip count
+                    const bool take = i < nkept && sm.list_d[i] < thr;
+                    warp_append(take, take ? sm.list_v[i] : 0u, sm.sel_v, &sc.nsel, c.tile, lane);
+                }
+            } else {
+                for (uint32_t wb = wlo + (tid & ~31u); wb <= whi; wb += T) {
+                    const uint32_t wd = wb + lane;
+                    const uint32_t bits = wd <= whi ? ld_relaxed(&c.bitmap[wd]) & range_mask(wd, lo, hi) : 0u;
+                    const uint32_t incl = warp_scan_incl((uint32_t)__popc(bits), lane);
+                    const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+                    for (uint32_t i0 = lane; i0 < total + lane; i0 += 32u * GATHER_G) {
+                        uint32_t vs[GATHER_G], ds[GATHER_G];
+#pragma unroll
+                        for (int g = 0; g < GATHER_G; ++g)
+                            vs[g] = nth_queued(wb, bits, incl, min(i0 + 32u * g, total - 1u));
+#pragma unroll
+                        for (int g = 0; g < GATHER_G; ++g)
+                            ds[g] = i0 + 32u * g < total ? (uint32_t)(__ldcg(&c.packed[vs[g]]) >> 32) : 0xFFFFFFFFu;
+#pragma unroll
+                        for (int g = 0; g < GATHER_G; ++g)
+                            warp_append(ds[g] < thr, vs[g], sm.sel_v, &sc.nsel, c.tile, lane);
+                    }
+                }
+            }
+            __syncthreads();
+            nsel = min(sc.nsel, c.tile);
+
+            // ---- C: take them off the inbox (acquire: the producers' packed-word
+            // updates are visible to the reads below); D: distances and row extents
+            uint32_t myclaim = 0;
+            for (uint32_t i = tid; i < nsel; i += T) {
+                uint32_t u = sm.sel_v[i];
+                const uint32_t bit = 1u << (u & 31u);
+                const uint32_t old = atom_and_acquire(&c.bitmap[u >> 5], ~bit);
+                uint32_t deg = 0, beg = 0, du = 0;
+                if (old & bit) {
+                    ++myclaim;
+                    du = (uint32_t)(__ldcg(&c.packed[u]) >> 32);
+                    beg = __ldg(&c.row_ptr[u]);
+                    deg = __ldg(&c.row_ptr[u + 1]) - beg;
+                    if (c.ids) sm.sel_v[i] = __ldg(&c.ids[u]);  // from here on sel_v holds predecessor labels
+                } else {
+                    sm.sel_v[i] = NONE;
+                }
+                sm.list_d[i] = du;
+                sm.list_v[i] = beg;
+                sm.sel_pref[i] = deg;
+            }
+            myclaim = warp_sum(myclaim);
+            if (lane == 0 && myclaim) atomicAdd(&sc.nclaim, myclaim);
         }
     }
     __syncthreads();
-    const uint32_t found = sc.cnt;
-    uint32_t nsel = 0, te = 0;
     if (found != 0) {
-        const uint32_t thr = bucket_bound<W>(sc.dmin, c.delta);
-        const uint32_t nkept = sc.nlist;
-
-        // ---- B: the near bucket, at most `tile` vertices: from the kept candidates,
-        // or, when there were more of them than the list holds, by enumerating the
-        // inbox again
-        if (nkept <= c.gcap) {
-            for (uint32_t i = tid; i < nkept + lane; i += T) {  // warp-uniform trip count
-                const bool take = i < nkept && sm.list_d[i] < thr;
-                warp_append(take, take ? sm.list_v[i] : 0u, sm.sel_v, &sc.nsel, c.tile, lane);
-            }
-        } else {
-            for (uint32_t wb = wlo + (tid & ~31u); wb <= whi; wb += T) {
-                const uint32_t wd = wb + lane;
-                const uint32_t bits = wd <= whi ? ld_relaxed(&c.bitmap[wd]) & range_mask(wd, lo, hi) : 0u;
-                const uint32_t incl = warp_scan_incl((uint32_t)__popc(bits), lane);
-                const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-                for (uint32_t i0 = lane; i0 < total + lane; i0 += 32u * GATHER_G) {
-                    uint32_t vs[GATHER_G], ds[GATHER_G];
-#pragma unroll
-                    for (int g = 0; g < GATHER_G; ++g)
-                        vs[g] = nth_queued(wb, bits, incl, min(i0 + 32u * g, total - 1u));
-#pragma unroll
-                    for (int g = 0; g < GATHER_G; ++g)
-                        ds[g] = i0 + 32u * g < total ? (uint32_t)(__ldcg(&c.packed[vs[g]]) >> 32) : 0xFFFFFFFFu;
-#pragma unroll
-                    for (int g = 0; g < GATHER_G; ++g)
-                        warp_append(ds[g] < thr, vs[g], sm.sel_v, &sc.nsel, c.tile, lane);
-                }
-            }
-        }
-        __syncthreads();
-        nsel = min(sc.nsel, c.tile);
-
-        // ---- C: take them off the inbox (acquire: the producers' packed-word
-        // updates are visible to the reads below); D: distances and row extents
-        uint32_t myclaim = 0;
-        for (uint32_t i = tid; i < nsel; i += T) {
-            uint32_t u = sm.sel_v[i];
-            const uint32_t bit = 1u << (u & 31u);
-            const uint32_t old = atom_and_acquire(&c.bitmap[u >> 5], ~bit);
-            uint32_t deg = 0, beg = 0, du = 0;
-            if (old & bit) {
-                ++myclaim;
-                du = (uint32_t)(__ldcg(&c.packed[u]) >> 32);
-                beg = __ldg(&c.row_ptr[u]);
-                deg = __ldg(&c.row_ptr[u + 1]) - beg;
-                if (c.ids) sm.sel_v[i] = __ldg(&c.ids[u]);  // from here on sel_v holds predecessor labels
-            } else {
-                sm.sel_v[i] = NONE;
-            }
-            sm.list_d[i] = du;
-            sm.list_v[i] = beg;
-            sm.sel_pref[i] = deg;
-        }
-        myclaim = warp_sum(myclaim);
-        if (lane == 0 && myclaim) atomicAdd(&sc.nclaim, myclaim);
-        __syncthreads();
         // Sub-rounds: a relaxation that lowers a vertex of this unit below the bucket
         // bound queues it in shared memory (lq) and the next sub-round relaxes it, with
         // no inbox bit and no rescan -- Dijkstra inside the partition (Alg. 3) until the
@@ -427,7 +601,8 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
                         if (key < old && (uint32_t)(old >> 32) > cc[j]) {
                             n_ai += 1u << 16;
                             // near and in this unit: relax it in the next sub-round
-                            if (!last && vv[j] >= lo && vv[j] < hi && cc[j] < thr) {
+                            const bool near = BK ? W::bucket(cc[j], c.delta) == bkb : cc[j] < thr;
+                            if (!last && vv[j] >= lo && vv[j] < hi && near) {
                                 const uint32_t pos = atomicAdd(&sc.nlq, 1u);
                                 if (pos < c.tile) {
                                     sm.lq[pos] = vv[j];
@@ -444,13 +619,25 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
                     n_ai = 0;
                 }
                 if (improved) {
-                    // every lowered word before any of this thread's inbox bits (release)
-                    __threadfence();
+                    // every lowered word before any of this thread's inbox bits (release);
+                    // with buckets the only reader is this block, after its barriers
+                    if constexpr (!BK) __threadfence();
 #pragma unroll
                     for (int j = 0; j < EDGE_BATCH; ++j) {
                         if (!(improved & (1u << j))) continue;
                         const uint32_t v = vv[j];
                         const uint32_t bit = 1u << (v & 31u);
+                        if constexpr (BK) {
+                            const uint32_t b = W::bucket(cc[j], c.delta);  // never below bkb
+                            const uint32_t kc = b / BK_NB, k0 = bkb / BK_NB;
+                            const uint32_t sl = kc == k0 ? b % BK_NB : kc <= k0 + BK_NC ? BK_NB + kc % BK_NC : BK_OV;
+                            if (!(atomicOr(&c.bitmap[(size_t)sl * c.words + (v >> 5)], bit) & bit)) {
+                                ++lact;
+                                atomicAdd(&sc.bk_cnt[sl], 1u);
+                            }
+                            if (sl == BK_OV) atomicMin(&sc.bk_ovmin, kc);
+                            continue;
+                        }
                         const uint32_t ob = atomicOr(&c.bitmap[v >> 5], bit);
                         if (!(ob & bit)) {
                             ++lact;
@@ -769,7 +956,7 @@ __global__ void __launch_bounds__(SOLVE_MAX_THREADS, 4) k_solve(SolveLaunch L) {
         c.packed = L.packed + (size_t)s * L.V;
         c.bitmap = L.bitmap + (size_t)s * L.words;
         c.dirty = L.dirty + (size_t)s * L.Q;
-        relax_round<W, true>(c, lo, hi, q, sm);
+        relax_round<W, true, false>(c, lo, hi, q, sm);
     }
     __syncthreads();
     flush_stats(L.hdr, sm.st);
@@ -810,22 +997,28 @@ __global__ void __launch_bounds__(SOLVE_MAX_THREADS, 4) k_batched(BatchLaunch L)
         c.w = L.w + P.edge_off;
         c.V = P.V;
         c.packed = L.packed + P.out_off;
-        c.bitmap = L.bitmap + P.bm_off;
         const uint32_t words = (P.V + 31u) / 32u;
+        c.words = words;
+        c.bitmap = L.bitmap + (size_t)BK_SLOTS * P.bm_off;  // the problem's fine, coarse and overflow bitmaps
         for (uint32_t i = tid; i < P.V; i += T) c.packed[i] = INF_KEY;
-        for (uint32_t i = tid; i < words; i += T) c.bitmap[i] = 0u;
+        for (uint32_t i = tid; i < BK_SLOTS * words; i += T) c.bitmap[i] = 0u;
+        if (tid < BK_SLOTS) sc.bk_cnt[tid] = 0u;
         __syncthreads();
         if (tid == 0) {
+            sc.bk_k0 = 0;
+            sc.bk_f = 0;
+            sc.bk_ovmin = 0xFFFFFFFFu;
             if (P.src < P.V) {
                 c.packed[P.src] = SRC_KEY;
-                c.bitmap[P.src >> 5] = 1u << (P.src & 31u);
+                c.bitmap[P.src >> 5] = 1u << (P.src & 31u);  // fine bucket 0
+                sc.bk_cnt[0] = 1u;
             } else {
                 set_status(L.hdr, SSSP_EINVAL);
             }
         }
         __syncthreads();
         for (;;) {
-            const uint32_t found = relax_round<W, false>(c, 0u, P.V, 0u, sm);
+            const uint32_t found = relax_round<W, false, true>(c, 0u, P.V, 0u, sm);
             if (tid == 0) {
                 int go = found != 0u;
                 if (go && globaltimer_ns() - t_begin > KERNEL_LIMIT_FACTOR * L.timeout_ns) {
@@ -929,6 +1122,8 @@ cudaError_t launch_solve(const SolveLaunch& L, cudaStream_t st) {
     }
     return cudaGetLastError();
 }
+
+uint32_t batched_bitmaps() { return BK_SLOTS; }
 
 cudaError_t batched_max_blocks_per_sm(int wtype, uint32_t threads, uint32_t tile, int* out) {
     const size_t smem = relax_smem_bytes(tile, 0);
