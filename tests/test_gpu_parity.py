@@ -395,6 +395,35 @@ def test_batched_parity_and_graph_replay(sssp):
     check()
 
 
+@pytest.mark.parametrize("f32,delta,tile", [(False, 1, 32), (False, 1000, 4096), (True, 0.01, 64), (True, 0.5, 1024),
+                                             (True, 50.0, 256)])
+def test_batched_buckets_extreme_widths_and_f32(sssp, f32, delta, tile):
+    # narrow buckets keep the coarse window and the overflow busy (splits, flushes, stale
+    # entries); one huge bucket degenerates to label correcting; float32 distances bucket by
+    # a rounded quotient
+    graphs, sources = [], []
+    for k in range(10):
+        n = 300 + 250 * k
+        ms = gg.member_seed(gg.BASE_SEED + 91, k)
+        if f32:
+            g0 = gg.rmat(ms, max(1, int(np.ceil(np.log2(n)))), 8 * n, n=n, wf32=(0.5, 2.0, 1e-4))
+        elif k % 2:
+            g0 = gg.erdos_renyi(ms, n, 8 * n, 1, 255)
+        else:
+            g0 = gg.rmat(ms, max(1, int(np.ceil(np.log2(n)))), 8 * n, n=n)
+        graphs.append(oracle.csr_of(g0))
+        sources.append(gg.pick_sources(ms, g0, 3))
+    b = sssp.Batch(graphs, sources, sssp.options(delta=delta, tile=tile))
+    b.solve()
+    st, _ = b.status()
+    assert st == sssp.SSSP_OK
+    for i in range(b.n_problems):
+        gi, s = int(b.prob_graph[i]), int(b.prob_source[i])
+        d, p, _ = oracle.dijkstra(graphs[gi], s)
+        bd, bp = b.result(i)
+        assert np.array_equal(u32(bd), d.view(np.uint32)) and np.array_equal(u32(bp), p), (i, gi, s)
+
+
 def test_batched_equals_single_solves(sssp):
     g0, srcs, _ = gg.workload_er16k()
     ref = oracle.csr_of(g0)
