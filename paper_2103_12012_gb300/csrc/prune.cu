@@ -1,8 +1,9 @@
 // K3 Trishla triangle prune (Sec. III.B, Algorithm 1).
 //
-// One warp per edge (u, v_i): it intersects the sorted adjacency lists N(u)
-// and N(v_i) -- lanes walk the shorter list and binary-search each entry in
-// the longer one -- and for every common head v_j tests
+// One warp per chunk of consecutive edges, 32 edges (u, v_i) at a time: for
+// each one whose v_i may be a witness, the warp intersects the sorted adjacency
+// lists N(u) and N(v_i) -- lanes walk the shorter list and binary-search each
+// entry in the longer one -- and for every common head v_j tests
 //     w(u, v_j) > w(u, v_i) + w(v_i, v_j).
 // A hit clears keep[(u, v_j)] and lowers witness[(u, v_j)] to v_i with
 // atomicMin, so the recorded witness is the smallest one whatever the
@@ -41,48 +42,72 @@ __device__ __forceinline__ bool dominated<WF32>(uint32_t w_uvj, uint32_t w_uvi, 
     return __uint_as_float(w_uvj) > __fadd_rn(__uint_as_float(w_uvi), __uint_as_float(w_vivj));
 }
 
+constexpr uint32_t TRISHLA_CHUNK = 1024;  // consecutive edges one warp takes (hub rows spread over warps)
+
+// the row (tail) of edge e: the largest r in [lo, hi) with row_ptr[r] <= e (row_ptr[lo] <= e)
+__device__ __forceinline__ uint32_t row_of(const uint32_t* row_ptr, uint32_t lo, uint32_t hi, uint32_t e) {
+    while (hi - lo > 1u) {
+        const uint32_t m = (lo + hi) >> 1;
+        if (__ldg(&row_ptr[m]) <= e)
+            lo = m;
+        else
+            hi = m;
+    }
+    return lo;
+}
+
 template <class W>
 __global__ void __launch_bounds__(256) k_trishla(uint32_t V, uint32_t E, unsigned long long B, int mode,
                                                  const uint32_t* __restrict__ row_ptr, const uint32_t* __restrict__ col,
                                                  const uint32_t* __restrict__ w, uint8_t* keep, uint32_t* witness) {
+    // One warp per chunk of TRISHLA_CHUNK consecutive edges: the lanes read 32 edges (u, v_i)
+    // at a time (their tails found inside the chunk's row range) and a ballot picks the ones
+    // whose v_i may serve as a witness (local mode: v_i in u's partition); for each of those
+    // the whole warp intersects N(u) with N(v_i), walking the shorter list and binary-searching
+    // the longer.
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t ei = warp; ei < E; ei += nwarps) {
-        // tail u of edge ei: last row whose start is <= ei
-        uint32_t lo = 0, hi = V;  // row_ptr[lo] <= ei < row_ptr[hi]
-        while (hi - lo > 1u) {
-            const uint32_t m = (lo + hi) >> 1;
-            if (__ldg(&row_ptr[m]) <= ei)
-                lo = m;
-            else
-                hi = m;
-        }
-        const uint32_t u = lo;
-        const uint32_t vi = __ldg(&col[ei]);
-        if (vi >= V) continue;
-        if (mode == 0 && (unsigned long long)vi / B != (unsigned long long)u / B) continue;
-        const uint32_t w_uvi = __ldg(&w[ei]);
-        const uint32_t a0 = __ldg(&row_ptr[u]), a1 = __ldg(&row_ptr[u + 1]);
-        const uint32_t b0 = __ldg(&row_ptr[vi]), b1 = __ldg(&row_ptr[vi + 1]);
-        if (a1 - a0 <= b1 - b0) {
-            // walk N(u), search N(v_i)
-            for (uint32_t j = a0 + lane; j < a1; j += 32u) {
-                const uint32_t vj = __ldg(&col[j]);
-                const uint32_t k = lower_bound_u32(col, b0, b1, vj);
-                if (k < b1 && __ldg(&col[k]) == vj && dominated<W>(__ldg(&w[j]), w_uvi, __ldg(&w[k]))) {
-                    keep[j] = 0;
-                    if (witness) atomicMin(&witness[j], vi);
-                }
-            }
-        } else {
-            // walk N(v_i), search N(u)
-            for (uint32_t k = b0 + lane; k < b1; k += 32u) {
-                const uint32_t vj = __ldg(&col[k]);
-                const uint32_t j = lower_bound_u32(col, a0, a1, vj);
-                if (j < a1 && __ldg(&col[j]) == vj && dominated<W>(__ldg(&w[j]), w_uvi, __ldg(&w[k]))) {
-                    keep[j] = 0;
-                    if (witness) atomicMin(&witness[j], vi);
+    const uint32_t nchunks = (E + TRISHLA_CHUNK - 1u) / TRISHLA_CHUNK;
+    for (uint32_t ch = warp; ch < nchunks; ch += nwarps) {
+        const uint32_t e0 = ch * TRISHLA_CHUNK, e1 = min(e0 + TRISHLA_CHUNK, E);
+        const uint32_t r0 = row_of(row_ptr, 0u, V, e0);
+        const uint32_t r1 = row_of(row_ptr, r0, V, e1 - 1u) + 1u;  // rows of the chunk: [r0, r1)
+        for (uint32_t base = e0; base < e1; base += 32u) {
+            const uint32_t ei = base + lane;
+            const bool in = ei < e1;
+            const uint32_t u = in ? row_of(row_ptr, r0, r1, ei) : r0;
+            const uint32_t vi = in ? __ldg(&col[ei]) : NONE;
+            const bool cand = vi < V && (mode != 0 || (unsigned long long)vi / B == (unsigned long long)u / B);
+            uint32_t ball = __ballot_sync(0xFFFFFFFFu, cand);
+            while (ball) {
+                const uint32_t f = __ffs(ball) - 1u;
+                ball &= ball - 1u;
+                const uint32_t uu = __shfl_sync(0xFFFFFFFFu, u, f);
+                const uint32_t v = __shfl_sync(0xFFFFFFFFu, vi, f);
+                const uint32_t w_uvi = __ldg(&w[base + f]);
+                const uint32_t a0 = __ldg(&row_ptr[uu]), a1 = __ldg(&row_ptr[uu + 1]);
+                const uint32_t b0 = __ldg(&row_ptr[v]), b1 = __ldg(&row_ptr[v + 1]);
+                if (a1 - a0 <= b1 - b0) {
+                    // walk N(u), search N(v_i)
+                    for (uint32_t j = a0 + lane; j < a1; j += 32u) {
+                        const uint32_t vj = __ldg(&col[j]);
+                        const uint32_t k = lower_bound_u32(col, b0, b1, vj);
+                        if (k < b1 && __ldg(&col[k]) == vj && dominated<W>(__ldg(&w[j]), w_uvi, __ldg(&w[k]))) {
+                            keep[j] = 0;
+                            if (witness) atomicMin(&witness[j], v);
+                        }
+                    }
+                } else {
+                    // walk N(v_i), search N(u)
+                    for (uint32_t k = b0 + lane; k < b1; k += 32u) {
+                        const uint32_t vj = __ldg(&col[k]);
+                        const uint32_t j = lower_bound_u32(col, a0, a1, vj);
+                        if (j < a1 && __ldg(&col[j]) == vj && dominated<W>(__ldg(&w[j]), w_uvi, __ldg(&w[k]))) {
+                            keep[j] = 0;
+                            if (witness) atomicMin(&witness[j], v);
+                        }
+                    }
                 }
             }
         }
@@ -100,7 +125,7 @@ cudaError_t prune_launch(const sssp_graph* g, int mode, uint8_t* keep, uint32_t*
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const unsigned long long B = ((unsigned long long)g->V + g->partitions - 1) / g->partitions;
-    const uint64_t want = ((uint64_t)g->E * 32 + 255) / 256;
+    const uint64_t want = (((uint64_t)g->E + TRISHLA_CHUNK - 1) / TRISHLA_CHUNK * 32 + 255) / 256;  // a warp per chunk
     const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)sms * 32));
     const uint32_t* w = static_cast<const uint32_t*>(g->w);
     if (g->wtype == SSSP_W_F32)
