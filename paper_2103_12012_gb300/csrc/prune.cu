@@ -42,7 +42,7 @@ __device__ __forceinline__ bool dominated<WF32>(uint32_t w_uvj, uint32_t w_uvi, 
     return __uint_as_float(w_uvj) > __fadd_rn(__uint_as_float(w_uvi), __uint_as_float(w_vivj));
 }
 
-constexpr uint32_t TRISHLA_CHUNK = 1024;  // consecutive edges one warp takes (hub rows spread over warps)
+constexpr uint32_t TRISHLA_CHUNK_MAX = 1024;  // consecutive edges one warp takes at most (hub rows spread over warps)
 
 // the row (tail) of edge e: the largest r in [lo, hi) with row_ptr[r] <= e (row_ptr[lo] <= e)
 __device__ __forceinline__ uint32_t row_of(const uint32_t* row_ptr, uint32_t lo, uint32_t hi, uint32_t e) {
@@ -57,10 +57,10 @@ __device__ __forceinline__ uint32_t row_of(const uint32_t* row_ptr, uint32_t lo,
 }
 
 template <class W>
-__global__ void __launch_bounds__(256) k_trishla(uint32_t V, uint32_t E, unsigned long long B, int mode,
+__global__ void __launch_bounds__(256) k_trishla(uint32_t V, uint32_t E, uint32_t chunk, unsigned long long B, int mode,
                                                  const uint32_t* __restrict__ row_ptr, const uint32_t* __restrict__ col,
                                                  const uint32_t* __restrict__ w, uint8_t* keep, uint32_t* witness) {
-    // One warp per chunk of TRISHLA_CHUNK consecutive edges: the lanes read 32 edges (u, v_i)
+    // One warp per chunk of `chunk` consecutive edges: the lanes read 32 edges (u, v_i)
     // at a time (their tails found inside the chunk's row range) and a ballot picks the ones
     // whose v_i may serve as a witness (local mode: v_i in u's partition); for each of those
     // the whole warp intersects N(u) with N(v_i), walking the shorter list and binary-searching
@@ -68,9 +68,9 @@ __global__ void __launch_bounds__(256) k_trishla(uint32_t V, uint32_t E, unsigne
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-    const uint32_t nchunks = (E + TRISHLA_CHUNK - 1u) / TRISHLA_CHUNK;
+    const uint32_t nchunks = (E + chunk - 1u) / chunk;
     for (uint32_t ch = warp; ch < nchunks; ch += nwarps) {
-        const uint32_t e0 = ch * TRISHLA_CHUNK, e1 = min(e0 + TRISHLA_CHUNK, E);
+        const uint32_t e0 = ch * chunk, e1 = min(e0 + chunk, E);
         const uint32_t r0 = row_of(row_ptr, 0u, V, e0);
         const uint32_t r1 = row_of(row_ptr, r0, V, e1 - 1u) + 1u;  // rows of the chunk: [r0, r1)
         for (uint32_t base = e0; base < e1; base += 32u) {
@@ -125,13 +125,16 @@ cudaError_t prune_launch(const sssp_graph* g, int mode, uint8_t* keep, uint32_t*
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const unsigned long long B = ((unsigned long long)g->V + g->partitions - 1) / g->partitions;
-    const uint64_t want = (((uint64_t)g->E + TRISHLA_CHUNK - 1) / TRISHLA_CHUNK * 32 + 255) / 256;  // a warp per chunk
+    // chunks: enough for about 64 warps per SM, between 32 and TRISHLA_CHUNK_MAX edges each
+    uint32_t chunk = 32;
+    while (chunk < TRISHLA_CHUNK_MAX && (uint64_t)g->E / (2ull * chunk) >= (uint64_t)sms * 64) chunk *= 2;
+    const uint64_t want = (((uint64_t)g->E + chunk - 1) / chunk * 32 + 255) / 256;  // a warp per chunk
     const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)sms * 32));
     const uint32_t* w = static_cast<const uint32_t*>(g->w);
     if (g->wtype == SSSP_W_F32)
-        k_trishla<WF32><<<grid, 256, 0, st>>>(g->V, g->E, B, mode, g->row_ptr, g->col, w, keep, witness);
+        k_trishla<WF32><<<grid, 256, 0, st>>>(g->V, g->E, chunk, B, mode, g->row_ptr, g->col, w, keep, witness);
     else
-        k_trishla<WU32><<<grid, 256, 0, st>>>(g->V, g->E, B, mode, g->row_ptr, g->col, w, keep, witness);
+        k_trishla<WU32><<<grid, 256, 0, st>>>(g->V, g->E, chunk, B, mode, g->row_ptr, g->col, w, keep, witness);
     return cudaGetLastError();
 }
 
