@@ -125,9 +125,9 @@ cudaError_t prune_launch(const sssp_graph* g, int mode, uint8_t* keep, uint32_t*
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const unsigned long long B = ((unsigned long long)g->V + g->partitions - 1) / g->partitions;
-    // chunks: enough for about 64 warps per SM, between 32 and TRISHLA_CHUNK_MAX edges each
+    // chunks: enough for about 128 warps per SM, between 32 and TRISHLA_CHUNK_MAX edges each
     uint32_t chunk = 32;
-    while (chunk < TRISHLA_CHUNK_MAX && (uint64_t)g->E / (2ull * chunk) >= (uint64_t)sms * 64) chunk *= 2;
+    while (chunk < TRISHLA_CHUNK_MAX && (uint64_t)g->E / (2ull * chunk) >= (uint64_t)sms * 128) chunk *= 2;
     const uint64_t want = (((uint64_t)g->E + chunk - 1) / chunk * 32 + 255) / 256;  // a warp per chunk
     const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)sms * 32));
     const uint32_t* w = static_cast<const uint32_t*>(g->w);
