@@ -225,6 +225,22 @@ struct Smem {
     unsigned long long* st;  // [ST_N] block statistics
 };
 
+// Sets v's inbox bit (the caller has fenced the lowered word before it); a new bit
+// counts as an activation and, in static mode, marks v's unit for a doorbell.
+template <bool STATIC>
+__device__ __forceinline__ void inbox_set(const Ctx& c, uint32_t v, uint32_t my_q, const Smem& sm, uint32_t& lact,
+                                          uint32_t& n_rem) {
+    const uint32_t bit = 1u << (v & 31u);
+    if (atomicOr(&c.bitmap[v >> 5], bit) & bit) return;
+    ++lact;
+    if (STATIC) {
+        const uint32_t p = v / c.B;
+        const uint32_t q = p * c.split + (v - p * c.B) / c.Bq;
+        if (q != my_q) ++n_rem;
+        atomicOr(&sm.touched[q >> 5], 1u << (q & 31u));
+    }
+}
+
 // One round over the unit owning vertices [lo, hi).  Returns the number of
 // queued vertices the scan found (0 = the unit's inbox was empty).
 template <class W, bool STATIC, bool BK>
@@ -537,116 +553,162 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
             uint32_t lact = 0, bad = 0;
             uint32_t n_ai = 0, n_rem = 0;  // statistics: atomics | improved << 16, remote activations
             const bool consec = te >= 32u * nsel;
+            // The read-first filter adds an L2 round trip before each atomic.  A sub-round
+            // of at most one edge per thread is latency-bound, so the persistent solve drops
+            // the filter there while this block's relaxations mostly reach the atomic (at
+            // least one atomic per four edges so far: wavefront graphs such as grids).
+            const bool filt = BK || te > T || sm.st[ST_ATOMICS] * 4u < sm.st[ST_EDGES];
             const uint32_t kstep = consec ? 1u : T;
             const uint32_t top = nsel > 1u ? 1u << (31 - __clz(nsel - 1u)) : 0u;
-            for (uint32_t k0 = consec ? tid * EDGE_BATCH : tid; k0 < te; k0 += EDGE_BATCH * T) {
-                uint32_t vv[EDGE_BATCH], cc[EDGE_BATCH], aa[EDGE_BATCH];
-#pragma unroll
-                for (int j = 0; j < EDGE_BATCH; ++j) aa[j] = 0;
-                if (consec) {
+            // A sub-round of at most one edge per thread is a chain of dependent global
+            // accesses.  There thread k takes edge k, and a vertex of this unit that it
+            // lowers below the bound has its row extents and label loaded alongside the
+            // atomic and goes straight into the upper half of the selection arrays
+            // (entries H.., free while nsel < H), so the next sub-round reads no global
+            // memory before its relaxations.
+            const uint32_t H = c.tile >> 1;
+            const bool small = !BK && te <= T && nsel < H;
+            if (small) {
+                if (tid < te) {
+                    uint32_t a = 0;
                     for (uint32_t st = top; st; st >>= 1)
-                        if (aa[0] + st < nsel && sm.sel_pref[aa[0] + st] <= k0) aa[0] += st;
-#pragma unroll
-                    for (int j = 1; j < EDGE_BATCH; ++j) {  // step over row ends; sel_pref[nsel] = te
-                        uint32_t a = aa[j - 1];
-                        while (a + 1u < nsel && sm.sel_pref[a + 1u] <= k0 + (uint32_t)j) ++a;
-                        aa[j] = a;
-                    }
-                } else {
-                    for (uint32_t st = top; st; st >>= 1) {
-#pragma unroll
-                        for (int j = 0; j < EDGE_BATCH; ++j) {
-                            const uint32_t m = aa[j] + st;
-                            if (m < nsel && sm.sel_pref[m] <= k0 + (uint32_t)j * T) aa[j] = m;
-                        }
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < EDGE_BATCH; ++j) {
-                    const uint32_t k = k0 + (uint32_t)j * kstep;
-                    vv[j] = NONE;
-                    if (k < te) {
-                        const uint32_t a = aa[j];
-                        const uint32_t e = sm.list_v[a] + (k - sm.sel_pref[a]);
-                        vv[j] = __ldg(&c.col[e]);
-                        cc[j] = __ldg(&c.w[e]);  // the weight, until it becomes the candidate below
-                    }
-                }
-                unsigned long long cur[EDGE_BATCH];
-#pragma unroll
-                for (int j = 0; j < EDGE_BATCH; ++j) {
-                    cur[j] = 0;
-                    if (vv[j] == NONE) continue;
-                    if (!W::weight_ok(cc[j]) || vv[j] >= c.V) {
+                        if (a + st < nsel && sm.sel_pref[a + st] <= tid) a += st;
+                    const uint32_t e = sm.list_v[a] + (tid - sm.sel_pref[a]);
+                    const uint32_t v = __ldg(&c.col[e]);
+                    uint32_t cand = __ldg(&c.w[e]);
+                    if (!W::weight_ok(cand) || v >= c.V) {
                         bad |= 1u;
-                        vv[j] = NONE;
-                        continue;
-                    }
-                    if (!W::add(sm.list_d[aa[j]], cc[j], cc[j])) {
+                    } else if (!W::add(sm.list_d[a], cand, cand)) {
                         bad |= 2u;
-                        vv[j] = NONE;
-                        continue;
-                    }
-                    // read-first filter: a stale (higher) value only lets a useless atomic through
-                    cur[j] = __ldcg(&c.packed[vv[j]]);
-                }
-                uint32_t improved = 0;
-#pragma unroll
-                for (int j = 0; j < EDGE_BATCH; ++j) {
-                    if (vv[j] == NONE) continue;
-                    const unsigned long long key = ((unsigned long long)cc[j] << 32) | sm.sel_v[aa[j]];
-                    if (key < cur[j]) {
-                        n_ai += 1u;
-                        const unsigned long long old = atomicMin(&c.packed[vv[j]], key);
-                        if (key < old && (uint32_t)(old >> 32) > cc[j]) {
-                            n_ai += 1u << 16;
-                            // near and in this unit: relax it in the next sub-round
-                            const bool near = BK ? W::bucket(cc[j], c.delta) == bkb : cc[j] < thr;
-                            if (!last && vv[j] >= lo && vv[j] < hi && near) {
-                                const uint32_t pos = atomicAdd(&sc.nlq, 1u);
-                                if (pos < c.tile) {
-                                    sm.lq[pos] = vv[j];
-                                    continue;
+                    } else {
+                        const bool mine = !last && v >= lo && v < hi && cand < thr;
+                        uint32_t beg = 0, end = 0, lab = v;
+                        if (mine) {
+                            beg = __ldg(&c.row_ptr[v]);
+                            end = __ldg(&c.row_ptr[v + 1]);
+                            if (c.ids) lab = __ldg(&c.ids[v]);
+                        }
+                        const unsigned long long key = ((unsigned long long)cand << 32) | sm.sel_v[a];
+                        if (key < (filt ? __ldcg(&c.packed[v]) : ~0ull)) {
+                            n_ai += 1u;
+                            const unsigned long long old = atomicMin(&c.packed[v], key);
+                            if (key < old && (uint32_t)(old >> 32) > cand) {
+                                n_ai += 1u << 16;
+                                const uint32_t pos = mine ? atomicAdd(&sc.nlq, 1u) : H;
+                                if (pos < H) {
+                                    sm.sel_v[H + pos] = lab;
+                                    sm.list_d[H + pos] = cand;
+                                    sm.list_v[H + pos] = beg;
+                                    sm.sel_pref[H + pos] = end - beg;
+                                } else {
+                                    __threadfence();  // the lowered word before its inbox bit
+                                    inbox_set<STATIC>(c, v, my_q, sm, lact, n_rem);
                                 }
                             }
-                            improved |= 1u << j;
                         }
                     }
                 }
-                if (n_ai & 0x80008000u) {  // keep both 16-bit halves from overflowing
-                    atomicAdd(&sm.st[ST_ATOMICS], (unsigned long long)(n_ai & 0xFFFFu));
-                    atomicAdd(&sm.st[ST_IMPROVED], (unsigned long long)(n_ai >> 16));
-                    n_ai = 0;
-                }
-                if (improved) {
-                    // every lowered word before any of this thread's inbox bits (release);
-                    // with buckets the only reader is this block, after its barriers
-                    if constexpr (!BK) __threadfence();
-#pragma unroll
-                    for (int j = 0; j < EDGE_BATCH; ++j) {
-                        if (!(improved & (1u << j))) continue;
-                        const uint32_t v = vv[j];
-                        const uint32_t bit = 1u << (v & 31u);
-                        if constexpr (BK) {
-                            const uint32_t b = W::bucket(cc[j], c.delta);  // never below bkb
-                            const uint32_t kc = b / BK_NB, k0 = bkb / BK_NB;
-                            const uint32_t sl = kc == k0 ? b % BK_NB : kc <= k0 + BK_NC ? BK_NB + kc % BK_NC : BK_OV;
-                            if (!(atomicOr(&c.bitmap[(size_t)sl * c.words + (v >> 5)], bit) & bit)) {
-                                ++lact;
-                                atomicAdd(&sc.bk_cnt[sl], 1u);
+            } else {
+                for (uint32_t k0 = consec ? tid * EDGE_BATCH : tid; k0 < te; k0 += EDGE_BATCH * T) {
+                    uint32_t vv[EDGE_BATCH], cc[EDGE_BATCH], aa[EDGE_BATCH];
+    #pragma unroll
+                    for (int j = 0; j < EDGE_BATCH; ++j) aa[j] = 0;
+                    if (consec) {
+                        for (uint32_t st = top; st; st >>= 1)
+                            if (aa[0] + st < nsel && sm.sel_pref[aa[0] + st] <= k0) aa[0] += st;
+    #pragma unroll
+                        for (int j = 1; j < EDGE_BATCH; ++j) {  // step over row ends; sel_pref[nsel] = te
+                            uint32_t a = aa[j - 1];
+                            while (a + 1u < nsel && sm.sel_pref[a + 1u] <= k0 + (uint32_t)j) ++a;
+                            aa[j] = a;
+                        }
+                    } else {
+                        for (uint32_t st = top; st; st >>= 1) {
+    #pragma unroll
+                            for (int j = 0; j < EDGE_BATCH; ++j) {
+                                const uint32_t m = aa[j] + st;
+                                if (m < nsel && sm.sel_pref[m] <= k0 + (uint32_t)j * T) aa[j] = m;
                             }
-                            if (sl == BK_OV) atomicMin(&sc.bk_ovmin, kc);
+                        }
+                    }
+    #pragma unroll
+                    for (int j = 0; j < EDGE_BATCH; ++j) {
+                        const uint32_t k = k0 + (uint32_t)j * kstep;
+                        vv[j] = NONE;
+                        if (k < te) {
+                            const uint32_t a = aa[j];
+                            const uint32_t e = sm.list_v[a] + (k - sm.sel_pref[a]);
+                            vv[j] = __ldg(&c.col[e]);
+                            cc[j] = __ldg(&c.w[e]);  // the weight, until it becomes the candidate below
+                        }
+                    }
+                    unsigned long long cur[EDGE_BATCH];
+    #pragma unroll
+                    for (int j = 0; j < EDGE_BATCH; ++j) {
+                        cur[j] = 0;
+                        if (vv[j] == NONE) continue;
+                        if (!W::weight_ok(cc[j]) || vv[j] >= c.V) {
+                            bad |= 1u;
+                            vv[j] = NONE;
                             continue;
                         }
-                        const uint32_t ob = atomicOr(&c.bitmap[v >> 5], bit);
-                        if (!(ob & bit)) {
-                            ++lact;
-                            if (STATIC) {
-                                const uint32_t p = v / c.B;
-                                const uint32_t q = p * c.split + (v - p * c.B) / c.Bq;
-                                if (q != my_q) ++n_rem;
-                                atomicOr(&sm.touched[q >> 5], 1u << (q & 31u));
+                        if (!W::add(sm.list_d[aa[j]], cc[j], cc[j])) {
+                            bad |= 2u;
+                            vv[j] = NONE;
+                            continue;
+                        }
+                        // read-first filter: a stale (higher) value only lets a useless atomic through
+                        cur[j] = filt ? __ldcg(&c.packed[vv[j]]) : ~0ull;
+                    }
+                    uint32_t improved = 0;
+    #pragma unroll
+                    for (int j = 0; j < EDGE_BATCH; ++j) {
+                        if (vv[j] == NONE) continue;
+                        const unsigned long long key = ((unsigned long long)cc[j] << 32) | sm.sel_v[aa[j]];
+                        if (key < cur[j]) {
+                            n_ai += 1u;
+                            const unsigned long long old = atomicMin(&c.packed[vv[j]], key);
+                            if (key < old && (uint32_t)(old >> 32) > cc[j]) {
+                                n_ai += 1u << 16;
+                                // near and in this unit: relax it in the next sub-round
+                                const bool near = BK ? W::bucket(cc[j], c.delta) == bkb : cc[j] < thr;
+                                if (!last && vv[j] >= lo && vv[j] < hi && near) {
+                                    const uint32_t pos = atomicAdd(&sc.nlq, 1u);
+                                    if (pos < c.tile) {
+                                        sm.lq[pos] = vv[j];
+                                        continue;
+                                    }
+                                }
+                                improved |= 1u << j;
                             }
+                        }
+                    }
+                    if (n_ai & 0x80008000u) {  // keep both 16-bit halves from overflowing
+                        atomicAdd(&sm.st[ST_ATOMICS], (unsigned long long)(n_ai & 0xFFFFu));
+                        atomicAdd(&sm.st[ST_IMPROVED], (unsigned long long)(n_ai >> 16));
+                        n_ai = 0;
+                    }
+                    if (improved) {
+                        // every lowered word before any of this thread's inbox bits (release);
+                        // with buckets the only reader is this block, after its barriers
+                        if constexpr (!BK) __threadfence();
+    #pragma unroll
+                        for (int j = 0; j < EDGE_BATCH; ++j) {
+                            if (!(improved & (1u << j))) continue;
+                            const uint32_t v = vv[j];
+                            if constexpr (BK) {
+                                const uint32_t bit = 1u << (v & 31u);
+                                const uint32_t b = W::bucket(cc[j], c.delta);  // never below bkb
+                                const uint32_t kc = b / BK_NB, k0 = bkb / BK_NB;
+                                const uint32_t sl = kc == k0 ? b % BK_NB : kc <= k0 + BK_NC ? BK_NB + kc % BK_NC : BK_OV;
+                                if (!(atomicOr(&c.bitmap[(size_t)sl * c.words + (v >> 5)], bit) & bit)) {
+                                    ++lact;
+                                    atomicAdd(&sc.bk_cnt[sl], 1u);
+                                }
+                                if (sl == BK_OV) atomicMin(&sc.bk_ovmin, kc);
+                                continue;
+                            }
+                            inbox_set<STATIC>(c, v, my_q, sm, lact, n_rem);
                         }
                     }
                 }
@@ -666,10 +728,18 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
                 if (bad) atomicOr(&sc.bad, bad);
             }
             __syncthreads();
-            const uint32_t nlq = min(sc.nlq, c.tile);
+            const uint32_t nlq = min(sc.nlq, small ? H : c.tile);
             if (nlq == 0) break;
             // the next sub-round's entries: the queued local vertices with fresh distances
+            // (small sub-round: as relaxed, moved down from the upper half)
             for (uint32_t i = tid; i < nlq; i += T) {
+                if (small) {
+                    sm.sel_v[i] = sm.sel_v[H + i];
+                    sm.list_d[i] = sm.list_d[H + i];
+                    sm.list_v[i] = sm.list_v[H + i];
+                    sm.sel_pref[i] = sm.sel_pref[H + i];
+                    continue;
+                }
                 const uint32_t u = sm.lq[i];
                 sm.sel_v[i] = c.ids ? __ldg(&c.ids[u]) : u;
                 sm.list_d[i] = (uint32_t)(__ldcg(&c.packed[u]) >> 32);
