@@ -241,6 +241,22 @@ __device__ __forceinline__ void inbox_set(const Ctx& c, uint32_t v, uint32_t my_
     }
 }
 
+// Batched buckets: files v (distance d, never below the current fine bucket bkb) in its
+// fine bucket, its coarse bucket or the overflow; a new bit counts as an activation.
+template <class W>
+__device__ __forceinline__ void bucket_file(const Ctx& c, uint32_t v, uint32_t d, uint32_t bkb, Scalars& sc,
+                                            uint32_t& lact) {
+    const uint32_t bit = 1u << (v & 31u);
+    const uint32_t b = W::bucket(d, c.delta);
+    const uint32_t kc = b / BK_NB, k0 = bkb / BK_NB;
+    const uint32_t sl = kc == k0 ? b % BK_NB : kc <= k0 + BK_NC ? BK_NB + kc % BK_NC : BK_OV;
+    if (!(atomicOr(&c.bitmap[(size_t)sl * c.words + (v >> 5)], bit) & bit)) {
+        ++lact;
+        atomicAdd(&sc.bk_cnt[sl], 1u);
+    }
+    if (sl == BK_OV) atomicMin(&sc.bk_ovmin, kc);
+}
+
 // One round over the unit owning vertices [lo, hi).  Returns the number of
 // queued vertices the scan found (0 = the unit's inbox was empty).
 template <class W, bool STATIC, bool BK>
@@ -567,7 +583,7 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
             // (entries H.., free while nsel < H), so the next sub-round reads no global
             // memory before its relaxations.
             const uint32_t H = c.tile >> 1;
-            const bool small = !BK && te <= T && nsel < H;
+            const bool small = te <= T && nsel < H;
             if (small) {
                 if (tid < te) {
                     uint32_t a = 0;
@@ -581,7 +597,8 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
                     } else if (!W::add(sm.list_d[a], cand, cand)) {
                         bad |= 2u;
                     } else {
-                        const bool mine = !last && v >= lo && v < hi && cand < thr;
+                        const bool mine = !last && v >= lo && v < hi &&
+                                          (BK ? W::bucket(cand, c.delta) == bkb : cand < thr);
                         uint32_t beg = 0, end = 0, lab = v;
                         if (mine) {
                             beg = __ldg(&c.row_ptr[v]);
@@ -600,6 +617,8 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
                                     sm.list_d[H + pos] = cand;
                                     sm.list_v[H + pos] = beg;
                                     sm.sel_pref[H + pos] = end - beg;
+                                } else if constexpr (BK) {
+                                    bucket_file<W>(c, v, cand, bkb, sc, lact);
                                 } else {
                                     __threadfence();  // the lowered word before its inbox bit
                                     inbox_set<STATIC>(c, v, my_q, sm, lact, n_rem);
@@ -696,19 +715,10 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
                         for (int j = 0; j < EDGE_BATCH; ++j) {
                             if (!(improved & (1u << j))) continue;
                             const uint32_t v = vv[j];
-                            if constexpr (BK) {
-                                const uint32_t bit = 1u << (v & 31u);
-                                const uint32_t b = W::bucket(cc[j], c.delta);  // never below bkb
-                                const uint32_t kc = b / BK_NB, k0 = bkb / BK_NB;
-                                const uint32_t sl = kc == k0 ? b % BK_NB : kc <= k0 + BK_NC ? BK_NB + kc % BK_NC : BK_OV;
-                                if (!(atomicOr(&c.bitmap[(size_t)sl * c.words + (v >> 5)], bit) & bit)) {
-                                    ++lact;
-                                    atomicAdd(&sc.bk_cnt[sl], 1u);
-                                }
-                                if (sl == BK_OV) atomicMin(&sc.bk_ovmin, kc);
-                                continue;
-                            }
-                            inbox_set<STATIC>(c, v, my_q, sm, lact, n_rem);
+                            if constexpr (BK)
+                                bucket_file<W>(c, v, cc[j], bkb, sc, lact);
+                            else
+                                inbox_set<STATIC>(c, v, my_q, sm, lact, n_rem);
                         }
                     }
                 }
