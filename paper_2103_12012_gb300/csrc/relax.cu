@@ -180,7 +180,9 @@ __device__ __forceinline__ uint32_t bucket_bound(uint32_t dmin, uint32_t delta) 
 }
 
 struct Scalars {
-    uint32_t cnt, nlist, dmin, nsel, nclaim, act, bad, nlq;
+    uint32_t cnt, nlist, dmin, nsel, nclaim, act, bad, te;
+    uint32_t nlq[2];  // local-queue counts of even and odd sub-rounds (a small sub-round ends
+                      // without the barrier after which one counter could be reset for the next)
     // batched buckets: current coarse bucket (absolute), current fine slot, least coarse
     // bucket in the overflow (a lower bound), this round's operation and slot, and the set
     // bits of each slot (fine, coarse, overflow)
@@ -548,15 +550,49 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
         // no inbox bit and no rescan -- Dijkstra inside the partition (Alg. 3) until the
         // bucket is exhausted or MAX_SUBROUNDS is reached.  Everything in lq is covered by
         // this round's reservation; whatever is left in lq at the end gets inbox bits.
+        // Small sub-rounds (below) alternate their entries between the lower and the
+        // upper half of the selection arrays: `base` is where this sub-round's are.
+        const uint32_t H = c.tile >> 1;
+        uint32_t base = 0;
         for (uint32_t sub = 0;; ++sub) {
-            te = block_scan_excl(sm.sel_pref, nsel, sm.wsum);
-            if (tid == 0) {
-                sm.sel_pref[nsel] = te;
-                sc.nlq = 0;
-                sm.st[ST_EDGES] += te;
+            if (nsel <= 32u) {  // one warp's scan, one barrier
+                if (tid < 32u) {
+                    const uint32_t x = lane < nsel ? sm.sel_pref[base + lane] : 0u;
+                    const uint32_t inc = warp_scan_incl(x, lane);
+                    if (lane < nsel) sm.sel_pref[base + lane] = inc - x;
+                    if (lane == 31u) {
+                        sm.sel_pref[base + nsel] = inc;
+                        sc.te = inc;
+                        sc.nlq[sub & 1u] = 0;
+                        sm.st[ST_EDGES] += inc;
+                    }
+                }
+                __syncthreads();
+                te = sc.te;
+            } else {
+                te = block_scan_excl(sm.sel_pref + base, nsel, sm.wsum);
+                if (tid == 0) {
+                    sm.sel_pref[base + nsel] = te;
+                    sc.nlq[sub & 1u] = 0;
+                    sm.st[ST_EDGES] += te;
+                }
+                __syncthreads();
             }
-            __syncthreads();
             const bool last = sub + 1u >= MAX_SUBROUNDS;
+            const bool small = te <= T && nsel < H;
+            if (!small && base) {
+                // the general path reads its entries from the lower half
+                for (uint32_t i = tid; i <= nsel; i += T) {
+                    if (i < nsel) {
+                        sm.sel_v[i] = sm.sel_v[H + i];
+                        sm.list_d[i] = sm.list_d[H + i];
+                        sm.list_v[i] = sm.list_v[H + i];
+                    }
+                    sm.sel_pref[i] = sm.sel_pref[H + i];
+                }
+                base = 0;
+                __syncthreads();
+            }
 
             // ---- E: relax all out-edges, edge-parallel.  Each thread keeps
             // EDGE_BATCH edges in flight together: all CSR loads, then all read-first
@@ -579,16 +615,15 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
             // A sub-round of at most one edge per thread is a chain of dependent global
             // accesses.  There thread k takes edge k, and a vertex of this unit that it
             // lowers below the bound has its row extents and label loaded alongside the
-            // atomic and goes straight into the upper half of the selection arrays
-            // (entries H.., free while nsel < H), so the next sub-round reads no global
-            // memory before its relaxations.
-            const uint32_t H = c.tile >> 1;
-            const bool small = te <= T && nsel < H;
+            // atomic and goes straight into the other half of the selection arrays (fewer
+            // than H entries each), so the next sub-round reads no global memory before its
+            // relaxations.
             if (small) {
+                const uint32_t nb = base ^ H;
                 if (tid < te) {
-                    uint32_t a = 0;
+                    uint32_t a = base;
                     for (uint32_t st = top; st; st >>= 1)
-                        if (a + st < nsel && sm.sel_pref[a + st] <= tid) a += st;
+                        if (a + st < base + nsel && sm.sel_pref[a + st] <= tid) a += st;
                     const uint32_t e = sm.list_v[a] + (tid - sm.sel_pref[a]);
                     const uint32_t v = __ldg(&c.col[e]);
                     uint32_t cand = __ldg(&c.w[e]);
@@ -611,12 +646,12 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
                             const unsigned long long old = atomicMin(&c.packed[v], key);
                             if (key < old && (uint32_t)(old >> 32) > cand) {
                                 n_ai += 1u << 16;
-                                const uint32_t pos = mine ? atomicAdd(&sc.nlq, 1u) : H;
-                                if (pos < H) {
-                                    sm.sel_v[H + pos] = lab;
-                                    sm.list_d[H + pos] = cand;
-                                    sm.list_v[H + pos] = beg;
-                                    sm.sel_pref[H + pos] = end - beg;
+                                const uint32_t pos = mine ? atomicAdd(&sc.nlq[sub & 1u], 1u) : H;
+                                if (pos + 1u < H) {
+                                    sm.sel_v[nb + pos] = lab;
+                                    sm.list_d[nb + pos] = cand;
+                                    sm.list_v[nb + pos] = beg;
+                                    sm.sel_pref[nb + pos] = end - beg;
                                 } else if constexpr (BK) {
                                     bucket_file<W>(c, v, cand, bkb, sc, lact);
                                 } else {
@@ -692,7 +727,7 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
                                 // near and in this unit: relax it in the next sub-round
                                 const bool near = BK ? W::bucket(cc[j], c.delta) == bkb : cc[j] < thr;
                                 if (!last && vv[j] >= lo && vv[j] < hi && near) {
-                                    const uint32_t pos = atomicAdd(&sc.nlq, 1u);
+                                    const uint32_t pos = atomicAdd(&sc.nlq[sub & 1u], 1u);
                                     if (pos < c.tile) {
                                         sm.lq[pos] = vv[j];
                                         continue;
@@ -738,18 +773,16 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
                 if (bad) atomicOr(&sc.bad, bad);
             }
             __syncthreads();
-            const uint32_t nlq = min(sc.nlq, small ? H : c.tile);
+            const uint32_t nlq = min(sc.nlq[sub & 1u], small ? H - 1u : c.tile);
             if (nlq == 0) break;
+            if (small) {  // the entries are in place already (as relaxed)
+                if (tid == 0) sm.st[ST_VERTS] += nlq;
+                nsel = nlq;
+                base ^= H;
+                continue;
+            }
             // the next sub-round's entries: the queued local vertices with fresh distances
-            // (small sub-round: as relaxed, moved down from the upper half)
             for (uint32_t i = tid; i < nlq; i += T) {
-                if (small) {
-                    sm.sel_v[i] = sm.sel_v[H + i];
-                    sm.list_d[i] = sm.list_d[H + i];
-                    sm.list_v[i] = sm.list_v[H + i];
-                    sm.sel_pref[i] = sm.sel_pref[H + i];
-                    continue;
-                }
                 const uint32_t u = sm.lq[i];
                 sm.sel_v[i] = c.ids ? __ldg(&c.ids[u]) : u;
                 sm.list_d[i] = (uint32_t)(__ldcg(&c.packed[u]) >> 32);
