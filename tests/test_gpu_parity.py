@@ -310,6 +310,43 @@ def test_solve_tiny_and_isolated(sssp):
     check_solve(sssp, g, ref, [0, 39, 2])
 
 
+def _subround_graph(f32):
+    """A path 0..9 (one edge per vertex: sub-rounds of one edge, whose entries alternate
+    between the halves of the selection arrays), a hub at 9 (1000 edges: a general
+    sub-round that follows a small one whose entries sit in the upper half), a fan of 200
+    at 5 whose heads each have two edges (a small sub-round of more than 32 vertices, with
+    heads lowered twice in one sub-round), and random heavier edges that relax nothing."""
+    rng = np.random.default_rng(77)
+    src, dst, w = [], [], []
+    def add(a, b, x):
+        src.append(a); dst.append(b); w.append(x)
+    for i in range(9):
+        add(i, i + 1, 1)
+    for j in range(1000):
+        add(9, 100 + j, 1 + j % 3)
+        add(100 + j, 2000 + j, 2)
+    for i in range(200):
+        add(5, 4000 + i, 7)
+        add(4000 + i, 5000 + i % 150, 1 + i % 5)
+        add(4000 + i, 5000 + (7 * i) % 150, 2)
+    for _ in range(3000):
+        add(int(rng.integers(0, 6000)), int(rng.integers(0, 6000)), int(rng.integers(200, 255)))
+    src, dst = np.array(src, np.uint32), np.array(dst, np.uint32)
+    w = np.array(w, np.float32) if f32 else np.array(w, np.uint32)
+    return src, dst, w
+
+
+@pytest.mark.parametrize("f32", [False, True])
+@pytest.mark.parametrize("P", [1, 4])
+@pytest.mark.parametrize("opts", [dict(delta=1e6), dict(delta=1e6, tile=256), dict()])
+def test_solve_small_and_general_subround_mix(sssp, f32, P, opts):
+    src, dst, w = _subround_graph(f32)
+    V = 6000
+    ref = oracle.csr(V, src, dst, w)
+    g = sssp.build_csr(V, src, dst, w, partitions=P)
+    check_solve(sssp, g, ref, [0, 9, 5, 4000], sssp.options(**opts))
+
+
 def test_solve_overflow_status(sssp):
     w = np.array([0xFFFFFFFE, 2, 1], np.uint32)
     src, dst = np.array([0, 1, 0], np.uint32), np.array([1, 2, 3], np.uint32)
@@ -435,6 +472,22 @@ def test_batched_equals_single_solves(sssp):
     for i in range(4):
         bd, bp = b.result(i)
         assert torch.equal(bd, dist[i]) and torch.equal(bp, pred[i])
+
+
+@pytest.mark.parametrize("f32", [False, True])
+@pytest.mark.parametrize("opts", [dict(delta=1e6), dict(delta=1e6, tile=256), dict(delta=1)])
+def test_batched_small_and_general_subround_mix(sssp, f32, opts):
+    src, dst, w = _subround_graph(f32)
+    ref = oracle.csr(6000, src, dst, w)
+    srcs = np.array([0, 9, 5, 4000], np.uint32)
+    b = sssp.Batch([ref, ref], [srcs, srcs[::-1].copy()], sssp.options(**opts))
+    b.solve()
+    st, _ = b.status()
+    assert st == sssp.SSSP_OK
+    for i, s in enumerate(list(srcs) + list(srcs[::-1])):
+        d, p, _ = oracle.dijkstra(ref, int(s))
+        bd, bp = b.result(i)
+        assert np.array_equal(u32(bd), d.view(np.uint32)) and np.array_equal(u32(bp), p), f"problem {i}"
 
 
 # ------------------------------------------------------------------------ K6
