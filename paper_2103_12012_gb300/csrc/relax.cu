@@ -28,7 +28,13 @@
 //      distance, set v's inbox bit after a release fence -- a message (Alg. 3
 //      send_msg) when v is in another unit; a vertex of this unit that falls
 //      below the bucket bound goes to a shared-memory queue instead and is
-//      relaxed by a sub-round of the same round (Dijkstra inside the unit);
+//      relaxed by a sub-round of the same round (Dijkstra inside the unit).
+//      A sub-round of at most one edge per thread (the wavefront of a
+//      high-diameter graph) is latency-bound: there a queued vertex's row
+//      extents are loaded alongside its atomic, its entry goes straight into
+//      the other half of the selection arrays, a single warp scans the degrees
+//      of up to 32 vertices, and the read-first filter is dropped while most
+//      relaxations of the block reach the atomic;
 //   F  settle the termination count and ring the doorbells of every unit
 //      that received a new vertex (and this unit's own if vertices are left).
 // Termination (Sec. III.D, the message counter of ToKa): `pending` counts
