@@ -351,7 +351,8 @@ def autotune(g: DeviceGraph, sources, base: SsspOptions | None = None, trials: i
     db = {}
     if cache and os.path.exists(path):
         try:
-            db = json.load(open(path))
+            with open(path) as f:
+                db = json.load(f)
         except ValueError:
             db = {}
     if key in db:
@@ -372,7 +373,8 @@ def autotune(g: DeviceGraph, sources, base: SsspOptions | None = None, trials: i
         db[key] = rec
         os.makedirs(os.path.dirname(path), exist_ok=True)
         tmp = path + ".tmp%d" % os.getpid()
-        json.dump(db, open(tmp, "w"), indent=1, sort_keys=True)
+        with open(tmp, "w") as f:
+            json.dump(db, f, indent=1, sort_keys=True)
         os.replace(tmp, path)
     return options(threads=rec["threads"], tile=rec["tile"], split=rec["split"], delta=rec["delta"]), rec["ms"]
 
@@ -472,11 +474,12 @@ class Batch:
             st, _ = self.status(stream)
             if st != SSSP_OK:
                 return float("inf")
+            s = torch.cuda.current_stream() if stream is None else stream
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
-            a.record()
+            a.record(s)
             self.solve(stream)
-            b.record()
+            b.record(s)
             st, _ = self.status(stream)
             return a.elapsed_time(b) if st == SSSP_OK else float("inf")
 
@@ -499,6 +502,9 @@ class Batch:
         return best, best_ms
 
     def make_plan(self, stream=None):
+        if self.plan is not None:
+            lib().sssp_batch_plan_destroy(self.plan)
+            self.plan = None
         h = ctypes.c_void_p()
         _check(lib().sssp_batch_plan_create(ctypes.byref(self.c), ctypes.byref(self.opts), _ptr(self.ws),
                                             self.ws_bytes, _stream(stream), ctypes.byref(h)), "sssp_batch_plan_create")
