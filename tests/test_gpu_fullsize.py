@@ -126,6 +126,61 @@ def test_er16k_prune_and_solve(sssp):
         check_invariants(graph, dist, pred, srcs.tolist())
 
 
+def test_rmat22_trishla_witnesses_and_sampled_completeness(sssp):
+    """Trishla (Algorithm 1, local mode) on the full R-MAT scale-22 graph with 148 partitions.
+    Every pruned edge (u, v_j) names a witness v_i in u's partition for which (u, v_i) and
+    (v_i, v_j) are edges and w(u, v_j) > w(u, v_i) + w(v_i, v_j); every kept edge names none.
+    On a seeded sample of edges the least witness found by brute force from that definition
+    (or none) equals the GPU's keep flag and witness."""
+    g0, _, P = gg.workload_rmat22()
+    g = sssp.build_csr(g0.V, g0.src, g0.dst, g0.w, partitions=P)
+    del g0
+    keep, wit = sssp.prune(g, 0)
+    V, E, NONE = g.V, g.E, 0xFFFFFFFF
+    B = -(-V // P)
+    rp = g.row_ptr.long()
+    deg = rp[1:] - rp[:-1]
+    tail = torch.repeat_interleave(torch.arange(V, device="cuda"), deg)
+    head = g.col.long()
+    w = g.w.long() & 0xFFFFFFFF
+    keys = tail * V + head
+    assert bool((keys[1:] > keys[:-1]).all())  # canonical CSR: rows sorted, no parallel edges
+    wt = wit.long() & 0xFFFFFFFF
+    pruned = keep == 0
+    assert bool((wt[~pruned] == NONE).all())
+
+    def edge_index(a, b):  # index of edge (a, b), or -1
+        k = a * V + b
+        i = torch.searchsorted(keys, k).clamp(max=E - 1)
+        return torch.where(keys[i] == k, i, torch.full_like(i, -1))
+
+    e = torch.nonzero(pruned).squeeze(1)
+    assert e.numel() > 0
+    u, vj, vi = tail[e], head[e], wt[e]
+    assert bool((vi < V).all()) and bool((vi // B == u // B).all())
+    e1, e2 = edge_index(u, vi), edge_index(vi, vj)
+    assert bool((e1 >= 0).all()) and bool((e2 >= 0).all())
+    assert bool((w[e] > w[e1] + w[e2]).all())
+    del e, u, vj, vi, e1, e2
+
+    rng = np.random.default_rng(2103)
+    se = torch.from_numpy(rng.choice(E, 20000, replace=False).astype(np.int64)).cuda()
+    su, sv = tail[se], head[se]
+    lens = deg[su]
+    pair = torch.repeat_interleave(torch.arange(se.numel(), device="cuda"), lens)
+    start = torch.cumsum(lens, 0) - lens
+    ce = rp[su][pair] + torch.arange(pair.numel(), device="cuda") - start[pair]  # edge (u, v_i)
+    ci = head[ce]
+    e2 = edge_index(ci, sv[pair])
+    ok = (ci // B == su[pair] // B) & (e2 >= 0)
+    ok &= w[se][pair] > w[ce] + torch.where(e2 >= 0, w[e2.clamp(min=0)], torch.zeros_like(e2))
+    least = torch.full((se.numel(),), NONE, dtype=torch.long, device="cuda")
+    least.scatter_reduce_(0, pair[ok], ci[ok], reduce="amin")
+    assert torch.equal(least, wt[se])
+    assert torch.equal(least != NONE, pruned[se])
+    assert int(pruned[se].sum()) > 0
+
+
 def test_rmat18_f32_forward_backward(sssp):
     g0, srcs, gup = gg.workload_rmat18_f32()
     ref = oracle.csr_of(g0)
