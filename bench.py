@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--split", type=int, default=0)
     ap.add_argument("--no-tune", action="store_true", help="library defaults instead of the autotuned schedule")
-    ap.add_argument("--profile-case", choices=["batched", "backward", "prune"],
+    ap.add_argument("--profile-case", choices=["batched", "backward", "prune", "grid"],
                     help="run a small case of one kernel three times and exit (for ncu captures)")
     return ap.parse_args()
 
@@ -643,7 +643,8 @@ def extras(sssp, dev):
 
 def profile_case(which):
     """Small cases of the other kernels for ncu: batched (64 graphs x 16 sources), backward (R-MAT scale 18
-    fp32, 32 sources), Trishla prune (R-MAT scale 16, local mode)."""
+    fp32, 32 sources), Trishla prune (R-MAT scale 16, local mode), and the solve on a 2048 x 2048 grid
+    from a corner (the high-diameter case, with the full grid's tuned schedule)."""
     import torch
 
     import paper_2103_12012_gb300 as sssp
@@ -665,6 +666,16 @@ def profile_case(which):
             gr = sssp.backward(g, pred, gd)
         torch.cuda.synchronize()
         print("backward", float(gr.abs().sum()))
+    elif which == "grid":
+        g0 = gg.grid(gg.BASE_SEED + 3, 2048, 2048, 1, 1000)
+        g = sssp.build_csr(g0.V, g0.src, g0.dst, g0.w, partitions=148)
+        solver = sssp.Solver(g, 1, sssp.options(delta=2982, tile=2048, split=4))
+        src = torch.zeros(1, dtype=torch.int32, device="cuda")
+        for _ in range(3):
+            solver.launch(src)
+        st, stats = solver.status()
+        assert st == sssp.SSSP_OK, st
+        print("grid", g.E, stats)
     else:
         g0 = gg.rmat(gg.BASE_SEED + 16, 16, 16 << 16)
         g = sssp.build_csr(g0.V, g0.src, g0.dst, g0.w, partitions=16)
