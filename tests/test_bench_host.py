@@ -55,3 +55,19 @@ def test_parse_clocks_median_and_reasons():
     hot = bench.parse_clocks("0, 1500, 2070, 1400, 0x40, Not Active, Active, Not Active, Not Active")
     assert hot["reasons"] == ["hw_thermal_slowdown"] and hot["sm_mhz"] == 1500.0
     assert bench.parse_clocks("")["samples"] == 0
+
+
+def test_cpu_baseline_single_all_cores_and_trishla():
+    """The bench's CPU baseline on a small R-MAT: the single-threaded oracle, the all-cores run
+    (one source per spawned process, over the saved CSR) and the oracle Trishla timing."""
+    import os
+
+    import graphgen as gg
+    g0 = gg.rmat(gg.BASE_SEED + 2, 12, 16 << 12, permute=True, wlo=1, whi=255)
+    srcs = gg.pick_sources(gg.BASE_SEED + 2, g0, 4)
+    out = bench.cpu_baseline(g0, srcs[:1], all_srcs=srcs)
+    assert out["kind"] == "oracle" and out["cores"] == 1 and out["value"] > 0
+    ac = out["all_cores"]
+    assert ac["cores"] == min(4, os.cpu_count() or 1) and ac["value"] > 0 and ac["unit"] == out["unit"]
+    tr = out["trishla_er16k"]
+    assert tr["edges"] == 131072 and tr["pruned"] > 0 and tr["s"] > 0
