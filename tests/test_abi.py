@@ -126,3 +126,26 @@ def test_update_host_checks_without_gpu(L):
     need = L.sssp_solve_workspace_size(ctypes.byref(g), 2, None)
     assert L.sssp_update(ctypes.byref(g), 2, 16, 16, 16, 1, None, 16, need - 1, None) == sssp.SSSP_ENOMEM
 
+
+
+def test_missing_library_raises(monkeypatch, tmp_path):
+    """No CPU fallback: without the built library every call fails loudly."""
+    monkeypatch.setattr(sssp, "_lib", None)
+    monkeypatch.setattr(sssp, "LIB_PATH", str(tmp_path / "libsssp.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        sssp.lib()
+
+
+def test_no_gpu_means_no_solve():
+    """On a machine without a GPU the binding raises instead of computing anywhere else."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import numpy as np
+    src = np.array([0, 1], np.uint32)
+    dst = np.array([1, 2], np.uint32)
+    w = np.array([3, 4], np.uint32)
+    with pytest.raises(RuntimeError, match="CUDA GPU"):
+        sssp.build_csr(3, src, dst, w)
+    with pytest.raises(RuntimeError, match="CUDA GPU"):
+        sssp.Batch([], [])
