@@ -298,8 +298,11 @@ sssp_status sssp_workspace_status(const void* ws, sssp_stream_t stream, sssp_sta
  *                sssp_status, copied on `stream` after the solve
  * Returns SSSP_ENOMEM (nothing launched) if sssp_solve_workspace_size(g, S, opt)
  * exceeds SSSP_NOALLOC_SCRATCH_BYTES.  The first call on a device resolves the
- * array's address (cudaGetSymbolAddress, with that device current); make it
- * before any stream capture.  All calls share the array, which keeps the last
+ * array's address (cudaGetSymbolAddress, with that device current) and caches
+ * it with the id of the device's current context; make it before any stream
+ * capture.  A call that finds another context current (after cudaDeviceReset,
+ * for instance) resolves the address again, so it too belongs outside a
+ * capture.  All calls share the array, which keeps the last
  * call's contents (each call re-initialises what it reads): calls that overlap
  * on the GPU race and must be ordered by the caller.
  */
@@ -340,7 +343,11 @@ size_t sssp_batch_workspace_size(const sssp_batch* b, const sssp_options* opt);
  * its problem alone -- init, Delta-ordered relaxation over the whole graph
  * (one partition), unpack -- with no message traffic between blocks.
  * Uploads the problem tables (host arrays) into ws on `stream` and waits for
- * that copy, then launches.
+ * that copy, then launches: unlike the other solve calls this one blocks the
+ * host until the upload is done, and it cannot be captured into a CUDA graph
+ * (the wait is not a stream operation).  The plan calls below upload once at
+ * creation and replay with no host work, so they are the path to use inside a
+ * capture or a loop.
  */
 sssp_status sssp_solve_batched(const sssp_batch* b, const sssp_options* opt, void* ws, size_t ws_bytes,
                                sssp_stream_t stream);
@@ -370,6 +377,10 @@ size_t sssp_backward_workspace_size(uint32_t V, uint32_t E, uint32_t S);
  * the tree, of which decreasing distance is one), accumulated in float64.
  *   pred      : device [S][V] canonical predecessors from sssp_solve
  *   grad_dist : device [S][V] float32 (values at unreachable vertices are ignored)
+ * The distances themselves are not an argument: the predecessor tree alone
+ * fixes which edges lie on each vertex's path, and the walk from every vertex
+ * up to its source visits children before parents without sorting by distance
+ * (an unreachable vertex, pred == 0xFFFFFFFF and not a source, starts no walk).
  *   grad_w    : device [E] float32 out, CSR edge order, summed over the S sources;
  *               non-tree edges get 0
  */

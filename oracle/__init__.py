@@ -14,6 +14,8 @@ Status of each function's parity pin:
   (brute force, library routines, closed forms, finite differences).
   layout -- pinned (a hand-worked order; brute-force order properties;
   distances invariant under the renaming).
+  compact -- pinned (a pure-Python construction from the canonical edge
+  dictionary, filtered by random, Trishla, empty and full keep masks).
 """
 from __future__ import annotations
 

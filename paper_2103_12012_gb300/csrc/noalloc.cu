@@ -12,8 +12,12 @@
 //
 // Rules of use:
 //  - The first call on a device looks up the array's device address with
-//    cudaGetSymbolAddress (with that device current) and caches it; make that
-//    first call before any stream capture.
+//    cudaGetSymbolAddress (with that device current) and caches it together
+//    with the id of the device's current CUDA context; make that first call
+//    before any stream capture.  A later call that finds another context
+//    current on the device (after cudaDeviceReset, for instance, which
+//    destroys the context and with it the array's old address) looks the
+//    address up again, so that call too belongs outside a capture.
 //  - Problems whose scratch would exceed SSSP_NOALLOC_SCRATCH_BYTES are
 //    rejected with SSSP_ENOMEM; nothing is launched.
 //  - Every call uses the same array, and the array keeps the previous call's
@@ -22,6 +26,8 @@
 //    without ordering) race on the array and give wrong results.
 //  - No cudaMalloc, cudaFree or allocating library routine is called.
 #include <mutex>
+
+#include <cuda.h>  // driver types only: the functions are reached through the runtime
 
 #include "common.cuh"
 #include "internal.h"
@@ -36,17 +42,48 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[SSSP_NOALLOC_SC
 constexpr int MAX_DEVICES = 64;
 std::mutex g_setup_mutex;
 void* g_scratch_ptr[MAX_DEVICES] = {};
+unsigned long long g_scratch_ctx[MAX_DEVICES] = {};  // id of the context the address belongs to
 
-// Once per device, with that device current: resolve the array's address.
+// Driver functions reached through the runtime (no link against libcuda): the current
+// context and its process-unique id.
+typedef CUresult (*ctx_get_current_fn)(CUcontext* ctx);
+typedef CUresult (*ctx_get_id_fn)(CUcontext ctx, unsigned long long* id);
+ctx_get_current_fn g_ctx_get_current = nullptr;
+ctx_get_id_fn g_ctx_get_id = nullptr;
+
+// Id of the context current on this thread, 0 if none is current (or ids are unavailable).
+unsigned long long current_ctx_id() {
+    if (!g_ctx_get_current) {
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+            return 0;
+        g_ctx_get_id = reinterpret_cast<ctx_get_id_fn>(f2);
+        g_ctx_get_current = reinterpret_cast<ctx_get_current_fn>(f1);
+    }
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (g_ctx_get_current(&ctx) != CUDA_SUCCESS || !ctx || g_ctx_get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// With the device current: the array's address in the device's current context, looked up
+// on the first call and again whenever the context has changed since.
 sssp_status scratch_for_current_device(void** out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return SSSP_ECUDA;
     if (dev < 0 || dev >= MAX_DEVICES) return SSSP_EUNSUPPORTED;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[dev]) {
+    const unsigned long long id = current_ctx_id();
+    if (!g_scratch_ptr[dev] || id == 0 || id != g_scratch_ctx[dev]) {
         void* p = nullptr;
+        // (also makes the device's primary context current if no context was)
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return SSSP_ECUDA;
         g_scratch_ptr[dev] = p;
+        g_scratch_ctx[dev] = current_ctx_id();
     }
     *out = g_scratch_ptr[dev];
     return SSSP_OK;

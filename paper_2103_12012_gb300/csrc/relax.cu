@@ -65,7 +65,13 @@ constexpr uint32_t IDLE_BACKOFF_MAX_NS = 1024;  // longest sleep of a block with
 // BK_NC coarse buckets of width BK_NB * delta after it, then one overflow
 constexpr uint32_t BK_NB = 16, BK_NC = 16, BK_OV = BK_NB + BK_NC, BK_SLOTS = BK_NB + BK_NC + 1;
 constexpr int EDGE_BATCH = 3;                // edges in flight per thread in phase E (measured: 2-4 similar)
-constexpr unsigned long long ROUND_RESERVE = 1ull << 32;  // termination counts reserved per round (> edges)
+// Termination counts a round reserves before any of its inbox bits can be visible.  A round
+// runs at most MAX_SUBROUNDS sub-rounds; a sub-round relaxes the edges of distinct vertices,
+// fewer than 2^32 (E is 32-bit), and turns on at most one inbox bit per relaxed edge, so a
+// round's activations stay below MAX_SUBROUNDS * 2^32 <= the reserve.  With fewer than 2^22
+// blocks in flight the 64-bit count cannot wrap.
+constexpr unsigned long long ROUND_RESERVE = 1ull << 41;
+static_assert(ROUND_RESERVE >= (unsigned long long)MAX_SUBROUNDS << 32, "reserve covers a round's activations");
 
 __device__ __forceinline__ uint32_t atom_and_acquire(uint32_t* p, uint32_t v) {
     uint32_t old;
@@ -186,7 +192,8 @@ __device__ __forceinline__ uint32_t bucket_bound(uint32_t dmin, uint32_t delta) 
 }
 
 struct Scalars {
-    uint32_t cnt, nlist, dmin, nsel, nclaim, act, bad, te;
+    uint32_t cnt, nlist, dmin, nsel, nclaim, bad, te;
+    unsigned long long act;  // inbox bits this round turned on (64-bit: see ROUND_RESERVE)
     uint32_t nlq[2];  // local-queue counts of even and odd sub-rounds (a small sub-round ends
                       // without the barrier after which one counter could be reset for the next)
     // batched buckets: current coarse bucket (absolute), current fine slot, least coarse
@@ -775,7 +782,7 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
                 }
             }
             if (lane == 0) {
-                if (lact) atomicAdd(&sc.act, lact);
+                if (lact) atomicAdd(&sc.act, (unsigned long long)lact);
                 if (bad) atomicOr(&sc.bad, bad);
             }
             __syncthreads();
@@ -807,7 +814,7 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
         if (STATIC) {
             if (tid == 0) {
                 const unsigned long long d =
-                    (unsigned long long)sc.act - ROUND_RESERVE - (unsigned long long)sc.nclaim;
+                    sc.act - ROUND_RESERVE - (unsigned long long)sc.nclaim;
                 atomicAdd(&c.hdr->pending, d);  // two's complement: adds act, returns reserve and takes
             }
             __threadfence();  // new bits (set before the barrier above) before the doorbells

@@ -101,6 +101,35 @@ def test_csr_f32_and_rejects_bad_endpoint():
 
 # --------------------------------------------------------------- partition
 
+@pytest.mark.parametrize("seed,mask", [(s, m) for s in range(3) for m in ("random", "trishla", "none", "all")])
+def test_compact_matches_dictionary_construction(seed, mask):
+    """oracle.compact against a pure-Python construction: the canonical edge dictionary (pins)
+    in sorted (tail, head) order, filtered by the keep mask, with row offsets counted per tail.
+    The masks: random, the dense-algebra Trishla keep mask (pins.trishla_dense, local mode),
+    nothing kept, everything kept."""
+    V, P = 40, 3
+    src, dst, w = _rand_graph(100 + seed, V, 300, 1, 9)
+    g = oracle.csr(V, src, dst, w)
+    best = pins.canonical_edges(V, src, dst, w)
+    keys = sorted(best)
+    if mask == "random":
+        keep = np.random.default_rng(seed).integers(0, 2, len(keys)).astype(np.uint8)
+    elif mask == "trishla":
+        dense = pins.trishla_dense(V, best, P, 0)
+        keep = np.array([dense[k][0] for k in keys], np.uint8)
+        assert 0 < keep.sum() < len(keys)
+    else:
+        keep = np.full(len(keys), 0 if mask == "none" else 1, np.uint8)
+    h = oracle.compact(g, keep)
+    kept = [k for k, f in zip(keys, keep.tolist()) if f]
+    row_ptr = [sum(1 for (a, _) in kept if a < u) for u in range(V + 1)]
+    assert h.V == V and h.E == len(kept)
+    assert h.row_ptr.tolist() == row_ptr
+    assert h.col.tolist() == [b for (_, b) in kept]
+    assert h.w.tolist() == [best[k][0] for k in kept]
+    assert h.eid.tolist() == [best[k][1] for k in kept]
+
+
 def test_partition_closed_forms():
     b, _ = oracle.partition(16384, 4)
     assert b.tolist() == [0, 4096, 8192, 12288, 16384]

@@ -26,12 +26,12 @@ def sssp():
     return m
 
 
-def _noalloc(sssp, g, sources_d, dist, pred, status):
+def _noalloc(sssp, g, sources_d, dist, pred, status, opts=None):
     gc = g.c()
-    opts = sssp.options()
+    opts = opts or sssp.options()
     st = sssp.lib().sssp_solve_noalloc(ctypes.byref(gc), ctypes.c_void_p(sources_d.data_ptr()), sources_d.numel(),
                                        ctypes.c_void_p(dist.data_ptr()), ctypes.c_void_p(pred.data_ptr()),
-                                       ctypes.byref(opts), ctypes.c_void_p(status.data_ptr()),
+                                       ctypes.byref(opts), None if status is None else ctypes.c_void_p(status.data_ptr()),
                                        sssp._stream())
     return st
 
@@ -65,3 +65,31 @@ def test_noalloc_rejects_problems_beyond_its_fixed_scratch(sssp):
     st = sssp.lib().sssp_solve_noalloc(ctypes.byref(gc), ctypes.c_void_p(dummy.data_ptr()), 1,
                                        ctypes.c_void_p(dummy.data_ptr()), None, None, None, sssp._stream())
     assert st == sssp.SSSP_ENOMEM
+
+
+def test_noalloc_reports_a_device_error_then_solves_again(sssp):
+    """The device-side status reaches status_out: a solve whose termination count is held one
+    above its true value must time out (SSSP_ETIMEOUT, after a 50 ms idle limit), and the next
+    call on the same fixed array, once without and once with a status word, is exact again."""
+    g0, _, P = gg.workload_er16k()
+    g = sssp.build_csr(g0.V, g0.src, g0.dst, g0.w, partitions=P)
+    srcs = np.array([0, 4567], np.uint32)
+    sources_d = torch.from_numpy(srcs.view(np.int32)).cuda()
+    ref_dist, ref_pred, st, _ = sssp.solve(g, srcs)
+    assert st == sssp.SSSP_OK
+    dist = torch.empty_like(ref_dist)
+    pred = torch.empty_like(ref_pred)
+    status = torch.full((1,), 99, dtype=torch.int32, device="cuda")
+    held = sssp.options(timeout_ns=50_000_000, flags=sssp.FLAG_TEST_HOLD_PENDING)
+    assert _noalloc(sssp, g, sources_d, dist, pred, status, held) == sssp.SSSP_OK  # launched
+    torch.cuda.synchronize()
+    assert int(status.item()) == sssp.SSSP_ETIMEOUT
+    dist.fill_(7)
+    assert _noalloc(sssp, g, sources_d, dist, pred, None) == sssp.SSSP_OK  # no status word
+    torch.cuda.synchronize()
+    assert torch.equal(dist, ref_dist) and torch.equal(pred, ref_pred)
+    dist.fill_(7)
+    assert _noalloc(sssp, g, sources_d, dist, pred, status) == sssp.SSSP_OK
+    torch.cuda.synchronize()
+    assert int(status.item()) == sssp.SSSP_OK
+    assert torch.equal(dist, ref_dist) and torch.equal(pred, ref_pred)
