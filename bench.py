@@ -20,7 +20,10 @@ roofline: the persistent relaxation kernel (launch timed alone with events
 
 Multi-GPU (torchrun): every rank solves its own 8 sources (weak scaling, no
 collective on the data path); value sums all ranks' edges over the slowest
-rank's time.
+rank's time.  The batched extra splits its (graph, source) problems over the
+ranks with the library's planner (no exchange) and the differentiable extra
+splits its sources and sums dL/dw with one all-reduce; the grid and
+warm-start extras run on rank 0.
 """
 from __future__ import annotations
 
@@ -53,12 +56,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched, differentiable and grid workloads")
+    ap.add_argument("--extras", default="", help="comma-separated subset of the extras to run (default: all)")
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--delta", type=float, default=0.0)
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--split", type=int, default=0)
     ap.add_argument("--no-tune", action="store_true", help="library defaults instead of the autotuned schedule")
-    ap.add_argument("--profile-case", choices=["batched", "backward", "prune", "grid"],
+    ap.add_argument("--profile-case", choices=["batched", "backward", "prune", "grid", "all"],
                     help="run a small case of one kernel three times and exit (for ncu captures)")
     return ap.parse_args()
 
@@ -98,6 +102,18 @@ def dram_traffic(edges_scanned):
     if sha != rec["code_sha256"]:
         return None, "kernel changed since the capture"
     return int(rec["dram_bytes_per_scanned_edge"] * edges_scanned), rec["capture"] + ", scaled by edges scanned"
+
+
+def batched_traffic(edges_scanned):
+    """DRAM bytes of one k_batched launch from the committed one-pass capture of the full batch,
+    scaled by edges scanned; None if there is no capture or the kernel code changed since."""
+    try:
+        rec = json.loads(open(os.path.join(ROOT, "profiles", "k_batched_dram_traffic.txt")).read())
+        if code_sha256(os.path.join(ROOT, rec["source"])) != rec["code_sha256"]:
+            return None
+    except (OSError, ValueError, KeyError):
+        return None
+    return int(rec["dram_bytes_per_scanned_edge"] * edges_scanned)
 
 
 def peaks():
@@ -173,7 +189,9 @@ def run_ours(a):
 
     ws, rank, local = dist_env()
     if ws > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        import datetime
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local),
+                                timeout=datetime.timedelta(seconds=600))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
@@ -291,6 +309,12 @@ def run_ours(a):
     achieved = alg_bytes / (relax_avg * 1e-3) / 1e9
     traffic, traffic_note = dram_traffic(stats["edges_scanned"])
 
+    # each frontier policy at its best bucket width (rank 0; outside the timed region)
+    policies = messages = None
+    if rank == 0 and not a.no_extras:
+        policies = policy_table(sssp, h, sources_d, opts, E_r)
+        messages = message_table(sssp, h, sources_d, opts, E_r)
+
     # end to end through the C ABI with host buffers
     e2e = None
     if not a.no_e2e:
@@ -314,6 +338,7 @@ def run_ours(a):
                              "sources and outputs in the generator's ids",
                    "options": {"threads": opts.threads or 512, "tile": opts.tile or 1024,
                                "delta": opts.delta or 4, "split": opts.split or 1,
+                               "policy": sssp.POLICY_NAMES[opts.policy],
                                "autotuned": not (a.no_tune or a.threads or a.tile or a.delta or a.split)}},
         "roofline": {"bound": "hbm", "kernel": "k_solve (persistent relaxation)", "achieved": round(achieved, 1),
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
@@ -328,14 +353,107 @@ def run_ours(a):
                    "prune_local_ms": round(prune_ms, 3), "pruned_edges": pruned, "edges": g.E,
                    "toka_threshold_interedges": inter_total, "toka_threshold_msgs": inter_total * P},
         "work": {"reached_edges": E_r, "reached_vertices": V_r, "stats_last_step": stats,
-                 "work_inflation": round(stats["edges_scanned"] / max(E_r, 1), 4)},
+                 "work_inflation": round(stats["edges_scanned"] / max(E_r, 1), 4),
+                 "policies": policies, "message_buffering": messages},
     }
-    if not a.no_extras and rank == 0:
-        line["extras"] = extras(sssp, dev)
+    if not a.no_extras:
+        ex = extras(sssp, dev, rank, ws, tuple(x for x in a.extras.split(",") if x))
+        if rank == 0:
+            line["extras"] = ex
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def policy_table(sssp, g, src_d, base, E_ref, reps=3):
+    """Each frontier policy at its best bucket width (a sweep over 1/64 .. 4 x the mean weight,
+    refined at 3/4 and 3/2 of the best, as the autotuner's) with the given tile and split: ms
+    per solve (CUDA events, median of `reps`) and the work inflation (edges scanned / E_ref).
+    A candidate whose first run takes over 3x the best so far is not repeated."""
+    import torch
+    w = g.w[:min(g.E, 65536)]
+    mean = float(w.float().mean()) if g.wtype == sssp.W_F32 else float((w.long() & 0xFFFFFFFF).double().mean())
+    factors = (1 / 64, 1 / 32, 1 / 16, 1 / 8, 1 / 4, 1 / 2, 1, 2, 4)
+    S = int(src_d.numel())
+    out = {}
+    best_all = None
+    def width(x):
+        return x if g.wtype == sssp.W_F32 else max(1.0, float(int(x)))
+
+    for pol, name in enumerate(sssp.POLICY_NAMES):
+        best = None
+        coarse = [width(mean * f) for f in factors] if pol != sssp.POLICY_ALL else [1.0]
+        for refine in (False, True):
+            if refine:  # 3/4 and 3/2 of the best width
+                if pol == sssp.POLICY_ALL or best is None:
+                    break
+                cands = [x for x in (width(best["delta"] * 0.75), width(best["delta"] * 1.5)) if x != best["delta"]]
+            else:
+                cands = coarse
+            for d in cands:
+                solver = sssp.Solver(g, S, sssp.options(threads=base.threads, tile=base.tile, split=base.split,
+                                                        delta=d, policy=pol))
+                a0, b0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a0.record()
+                solver.launch(src_d)
+                b0.record()
+                st, stats = solver.status()
+                if st != sssp.SSSP_OK:
+                    continue
+                first = a0.elapsed_time(b0)
+                if best_all is not None and first > 3 * best_all:  # far off the pace: one untimed run is enough
+                    if best is None or first < best["ms"]:
+                        best = {"delta": d, "ms": round(first, 3), "work_inflation": round(stats["edges_scanned"] / E_ref, 3),
+                                "rounds": stats["rounds"], "single_run": True}
+                    continue
+                times = []
+                for _ in range(reps):
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record()
+                    solver.launch(src_d)
+                    b.record()
+                    torch.cuda.synchronize()
+                    times.append(a.elapsed_time(b))
+                ms = statistics.median(times)
+                if best is None or ms < best["ms"]:
+                    best = {"delta": d, "ms": round(ms, 3), "work_inflation": round(stats["edges_scanned"] / E_ref, 3),
+                            "rounds": stats["rounds"]}
+                best_all = ms if best_all is None else min(best_all, ms)
+                del solver
+        out[name] = best
+    return out
+
+
+def message_table(sssp, g, src_d, base, E_ref, sizes=(0, 1, 8, 32), reps=3):
+    """Message buffering (msg_buffer: 0 = direct, k = a warp pushes its held messages out at k and
+    at the end of each sub-round) at the given schedule: ms per solve (CUDA events, median of
+    `reps`), work inflation (edges scanned / E_ref) and rounds."""
+    import torch
+    S = int(src_d.numel())
+    out = {}
+    for k in sizes:
+        o = sssp.options(threads=base.threads, tile=base.tile, split=base.split, delta=base.delta,
+                         policy=base.policy, msg_buffer=k)
+        solver = sssp.Solver(g, S, o)
+        solver.launch(src_d)
+        st, stats = solver.status()
+        if st != sssp.SSSP_OK:
+            out[str(k)] = {"error": sssp.status_string(st)}
+            continue
+        times = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            solver.launch(src_d)
+            b.record()
+            torch.cuda.synchronize()
+            times.append(a.elapsed_time(b))
+        out[str(k)] = {"ms": round(statistics.median(times), 3),
+                       "work_inflation": round(stats["edges_scanned"] / E_ref, 3), "rounds": stats["rounds"],
+                       "remote_activations": stats["remote_activations"]}
+        del solver
+    return out
 
 
 def run_e2e(sssp, g, srcs, opts, dev, E_r, steps):
@@ -510,11 +628,16 @@ def _time_ms(fn, reps):
     return a.elapsed_time(b) / reps
 
 
-def extras_batched(sssp, dev):
+def extras_batched(sssp, dev, rank=0, world=1):
     """512 graphs x 16 sources: one CUDA-graph replay of the batched kernel vs per-problem sssp_solve
-    launches (one source each) and per-graph launches (16 sources each), same options."""
+    launches (one source each) and per-graph launches (16 sources each), same options.  With
+    several ranks each solves the (graph, source) problems the library's planner gives it
+    (split by estimated edges, no exchange); the times are reduced by the caller (MAX)."""
     import torch
     graphs0, sources = gg.workload_batch512()
+    if world > 1:
+        keep_g, sources = sssp.shard_batch(graphs0, sources, rank, world)
+        graphs0 = [graphs0[i] for i in keep_g]
     # the per-solve baseline gets a partition count that spreads one graph over many blocks
     graphs = [sssp.build_csr(g.V, g.src, g.dst, g.w, partitions=max(1, min(148, g.V // 512))) for g in graphs0]
     del graphs0
@@ -527,6 +650,20 @@ def extras_batched(sssp, dev):
     st, stats = b.status()
     assert st == sssp.SSSP_OK, sssp.status_string(st)
     ms_plan = _time_ms(b.replay, 3)
+    # algorithmic bytes of the replay: per problem 8 per reached edge + 16 per reached vertex
+    E_r = V_r = 0
+    by_graph = {}
+    for i in range(b.n_problems):
+        by_graph.setdefault(int(b.prob_graph[i]), []).append(i)
+    for gi, probs in by_graph.items():
+        gd = graphs[gi]
+        deg = (gd.row_ptr[1:].long() - gd.row_ptr[:-1].long())
+        reached = torch.stack([b.result(i)[0] for i in probs]) != -1
+        E_r += int((reached.long() * deg[None, :]).sum())
+        V_r += int(reached.sum())
+    alg = 8 * E_r + 16 * V_r
+    peak, peak_kind = peaks()
+    achieved = alg / (ms_plan * 1e-3) / 1e9
     # per-graph launches (16 sources in one sssp_solve each)
     solvers = [(sssp.Solver(g, len(s)), torch.from_numpy(s.view(np.int32)).to(dev)) for g, s in zip(graphs, sources)]
     ms_graph = _time_ms(lambda: [sv.launch(src) for sv, src in solvers], 1)
@@ -542,15 +679,25 @@ def extras_batched(sssp, dev):
             "problems": n_prob, "edges_total": int(edges),
             "options": {"delta": tuned.delta, "tile": tuned.tile or 1024, "autotuned": True},
             "graph_replay_ms": round(ms_plan, 3), "solves_per_s": round(n_prob / ms_plan * 1e3, 1),
+            "reached_edges": E_r, "reached_vertices": V_r, "edges_scanned": stats["edges_scanned"],
+            "work_inflation": round(stats["edges_scanned"] / max(E_r, 1), 3),
+            "roofline": {"bound": "hbm", "kernel": "k_batched", "achieved": round(achieved, 1), "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                         "alg_bytes_per_launch": alg, "traffic": batched_traffic(stats["edges_scanned"])},
             "per_graph_launches_ms": round(ms_graph, 3), "per_problem_launches_ms": round(ms_prob, 3),
             "speedup_vs_per_problem": round(ms_prob / ms_plan, 3),
             "speedup_vs_per_graph": round(ms_graph / ms_plan, 3)}
 
 
-def extras_differentiable(sssp, dev):
-    """R-MAT scale 18, fp32 weights, 32 sources: forward solve, backward, forward+backward."""
+def extras_differentiable(sssp, dev, rank=0, world=1):
+    """R-MAT scale 18, fp32 weights, 32 sources: forward solve, backward, forward+backward.  With
+    several ranks each takes its share of the sources (the planner deals them out) and dL/dw is
+    summed over the ranks by one all-reduce, inside the backward's timing."""
     import torch
     g0, srcs, gup = gg.workload_rmat18_f32()
+    if world > 1:
+        idx = sssp.shard_sources(len(srcs), rank, world)
+        srcs, gup = srcs[idx], gup[idx]
     # 16 partitions: 512 units for the 32 sources keep the persistent blocks busy
     g = sssp.build_csr(g0.V, g0.src, g0.dst, g0.w, partitions=16)
     src_d = torch.from_numpy(srcs.view(np.int32)).to(dev)
@@ -560,18 +707,53 @@ def extras_differentiable(sssp, dev):
     solver.launch(src_d)
     st, _ = solver.status()
     assert st == sssp.SSSP_OK
+
+    def bwd():
+        return sssp.allreduce_sum(sssp.backward(g, solver.pred, gup_d))
     ms_fwd = _time_ms(lambda: solver.launch(src_d), 5)
-    ms_bwd = _time_ms(lambda: sssp.backward(g, solver.pred, gup_d), 5)
-    ms_both = _time_ms(lambda: (solver.launch(src_d), sssp.backward(g, solver.pred, gup_d)), 5)
+    ms_bwd = _time_ms(bwd, 5)
+    ms_both = _time_ms(lambda: (solver.launch(src_d), bwd()), 5)
     return {"workload": "rmat-s18-ef8 fp32 weights, 32 sources, 16 partitions",
+            "sources_this_rank": int(len(srcs)),
             "options": {"delta": opts.delta, "tile": opts.tile, "split": opts.split, "autotuned": True},
             "forward_ms": round(ms_fwd, 3),
             "backward_ms": round(ms_bwd, 3), "forward_backward_ms": round(ms_both, 3),
             "fwd_bwd_over_fwd": round(ms_both / ms_fwd, 3)}
 
 
+def tree_depth(pred):
+    """Edges on the longest tree path (the hops of the deepest shortest path) of each predecessor
+    row, by pointer doubling on the device."""
+    import torch
+    p = pred.long() & 0xFFFFFFFF
+    none = p == 0xFFFFFFFF
+    anc = torch.where(none, torch.arange(p.shape[-1], device=p.device).expand_as(p), p)
+    dep = (~none).long()
+    for _ in range(int(p.shape[-1]).bit_length()):
+        dep = dep + torch.gather(dep, -1, anc) * (anc != torch.gather(anc, -1, anc)).long()
+        anc = torch.gather(anc, -1, anc)
+    return dep.max(dim=-1).values
+
+
+def chain_ms_per_hop(sssp, dev, n=1 << 16, partitions=1, reps=3):
+    """ms per hop of a pure chain 0 -> 1 -> ... -> n-1 (unit weights): every hop waits for the one
+    before it, inside one unit (partitions=1: a sub-round each) or crossing units."""
+    import torch
+    v = np.arange(n - 1, dtype=np.uint32)
+    g = sssp.build_csr(n, v, v + 1, np.ones(n - 1, np.uint32), partitions=partitions)
+    solver = sssp.Solver(g, 1, sssp.options(delta=1e9))
+    src = torch.zeros(1, dtype=torch.int32, device=dev)
+    solver.launch(src)
+    st, _ = solver.status()
+    assert st == sssp.SSSP_OK
+    return statistics.median(_time_ms(lambda: solver.launch(src), 1) for _ in range(reps)) / (n - 1)
+
+
 def extras_grid(sssp, dev):
-    """4096 x 4096 grid, corner source: the high-diameter case (autotuned schedule)."""
+    """4096 x 4096 grid, corner source: the high-diameter case (autotuned schedule).  Latency model:
+    the deepest shortest path has `depth` hops, each of which waits for the one before it; a pure
+    chain solved inside one unit gives the least time per hop this solve takes (one sub-round),
+    so depth x that time is the floor of the grid's solve in this design."""
     import torch
     g0, srcs, P = gg.workload_grid4096()
     g = sssp.build_csr(g0.V, g0.src, g0.dst, g0.w, partitions=P)
@@ -583,10 +765,19 @@ def extras_grid(sssp, dev):
     st, stats = solver.status()
     assert st == sssp.SSSP_OK
     ms = _time_ms(lambda: solver.launch(src_d), 3)
+    depth = int(tree_depth(solver.pred)[0].item())
+    hop_in = chain_ms_per_hop(sssp, dev, partitions=1)
+    hop_cross = chain_ms_per_hop(sssp, dev, partitions=148)
+    model = {"depth_hops": depth, "ms_per_hop": round(ms / depth, 6),
+             "chain_ms_per_hop_in_unit": round(hop_in, 6), "chain_ms_per_hop_148_units": round(hop_cross, 6),
+             "floor_ms": round(depth * hop_in, 3), "measured_over_floor": round(ms / (depth * hop_in), 2)}
     return {"workload": "grid 4096x4096, corner source", "delta": opts.delta, "tile": opts.tile,
-            "split": opts.split, "ms": round(ms, 3),
+            "latency_model": model,
+            "split": opts.split, "policy": sssp.POLICY_NAMES[opts.policy], "ms": round(ms, 3),
             "gteps": round(g.E / (ms * 1e-3) / 1e9, 4), "rounds": stats["rounds"],
-            "work_inflation": round(stats["edges_scanned"] / g.E, 3)}
+            "work_inflation": round(stats["edges_scanned"] / g.E, 3),
+            "policies": policy_table(sssp, g, src_d, opts, g.E),
+            "message_buffering": message_table(sssp, g, src_d, opts, g.E)}
 
 
 def extras_warm(sssp, dev):
@@ -632,16 +823,101 @@ def extras_warm(sssp, dev):
             "fresh_edges_scanned": fresh["edges_scanned"], "equal_to_fresh": equal}
 
 
-def extras(sssp, dev):
+_SHARDED_KEYS = {"batched": ["graph_replay_ms", "per_graph_launches_ms", "per_problem_launches_ms", "problems",
+                               "edges_total"],
+                 "differentiable": ["forward_ms", "backward_ms", "forward_backward_ms", "sources_this_rank"]}
+
+
+def _reduce_sharded(name, d, world, dev):
+    """Across ranks: times (keys ending in _ms) by MAX, problem counts by SUM; rates recomputed.
+    Every rank reduces the same keys (NaN where its extra failed), so the collectives match."""
+    import torch
+    import torch.distributed as dist
+    if world == 1:
+        return d
+    keys = _SHARDED_KEYS[name]
+    t = torch.tensor([float(d.get(k, float("nan"))) for k in keys], dtype=torch.float64, device=dev)
+    mx, sm = t.clone(), t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    out = dict(d)
+    if any(np.isnan(t.tolist())) or "error" in d:
+        out["error"] = out.get("error", "an extra failed on another rank")
+        return out
+    for i, k in enumerate(keys):
+        out[k] = round(float(mx[i] if k.endswith("_ms") else sm[i]), 3)
+    if "graph_replay_ms" in out:
+        out["solves_per_s"] = round(out["problems"] / out["graph_replay_ms"] * 1e3, 1)
+        out["speedup_vs_per_problem"] = round(out["per_problem_launches_ms"] / out["graph_replay_ms"], 3)
+        out["speedup_vs_per_graph"] = round(out["per_graph_launches_ms"] / out["graph_replay_ms"], 3)
+    if "forward_ms" in out:
+        out["fwd_bwd_over_fwd"] = round(out["forward_backward_ms"] / out["forward_ms"], 3)
+    out["ranks"] = world
+    out["sharding"] = "problems split by estimated edges (sssp_shard_problems), no exchange" if \
+        "graph_replay_ms" in out else "sources dealt out over the ranks; dL/dw summed by one all-reduce"
+    return out
+
+
+def extras_prune_overlap(sssp, dev):
+    """Trishla on the solve's idle time (sssp_solve_prune) against a solve followed by a separate
+    prune (sssp_solve + sssp_prune), local mode, on the 16K ER workload, R-MAT scale 22 (8
+    sources, locality layout) and the 4096 x 4096 grid (no triangles: nothing to prune, but the
+    blocks are idle most of the solve).  Same options for both; CUDA events, median of 3."""
+    import torch
+
+    def med(fn, reps=3):
+        return statistics.median(_time_ms(fn, 1) for _ in range(reps))
+
     out = {}
-    for name, fn in (("batched", extras_batched), ("differentiable", extras_differentiable), ("grid", extras_grid),
-                     ("warm_start", extras_warm)):
+    cases = (("er16k", lambda: gg.workload_er16k(), False), ("rmat22", lambda: gg.workload_rmat22(), True),
+             ("grid4096", lambda: gg.workload_grid4096(), False))
+    for name, make, lay in cases:
+        g0, srcs, P = make()
+        g = sssp.build_csr(g0.V, g0.src, g0.dst, g0.w, partitions=P)
+        del g0
+        if lay:
+            g = sssp.layout(g)
+        src_d = torch.from_numpy(np.asarray(srcs, np.uint32).view(np.int32)).to(dev)
+        opts, _ = sssp.autotune(g, src_d)
+        solver = sssp.Solver(g, len(srcs), opts)
+        keep = torch.empty(max(g.E, 1), dtype=torch.uint8, device=dev)
+        solver.launch_prune(src_d, 0, keep)
+        st, _ = solver.status()
+        assert st == sssp.SSSP_OK
+        k_sep, _ = sssp.prune(g, 0, witness=False)
+        assert torch.equal(k_sep, keep[:g.E])
+        t_solve = med(lambda: solver.launch(src_d))
+        t_prune = med(lambda: sssp.prune(g, 0, witness=False))
+        t_both = med(lambda: solver.launch_prune(src_d, 0, keep))
+        out[name] = {"solve_ms": round(t_solve, 3), "prune_ms": round(t_prune, 3),
+                     "solve_then_prune_ms": round(t_solve + t_prune, 3), "solve_prune_ms": round(t_both, 3),
+                     "hidden_ms": round(t_solve + t_prune - t_both, 3), "pruned_edges": int((k_sep == 0).sum()),
+                     "edges": g.E}
+        del solver, keep, k_sep, g
+        torch.cuda.empty_cache()
+    return out
+
+
+def extras(sssp, dev, rank=0, world=1, only=()):
+    """The other workloads.  batched and differentiable run on every rank, sharded, and are reduced
+    over the ranks; grid and warm_start (one graph, one solve) run on rank 0 only."""
+    import torch.distributed as dist
+    out = {}
+    for name, fn, sharded in (("batched", extras_batched, True), ("differentiable", extras_differentiable, True),
+                              ("grid", extras_grid, False), ("warm_start", extras_warm, False),
+                              ("prune_overlap", extras_prune_overlap, False)):
+        if (not sharded and rank != 0) or (only and name not in only):
+            continue
         t0 = time.perf_counter()
         try:
-            out[name] = fn(sssp, dev)
+            out[name] = fn(sssp, dev, rank, world) if sharded else fn(sssp, dev)
         except Exception as e:  # an extra must not hide the headline line
             out[name] = {"error": repr(e)[:300]}
+        if sharded:
+            out[name] = _reduce_sharded(name, out[name], world, dev)
         out[name]["wall_s"] = round(time.perf_counter() - t0, 1)
+    if world > 1:
+        dist.barrier()
     return out
 
 
@@ -652,7 +928,48 @@ def profile_case(which):
     import torch
 
     import paper_2103_12012_gb300 as sssp
-    if which == "batched":
+    if which == "all":
+        # every kernel of the library once (CSR build, partition, layout, Trishla, compact, solve with
+        # its init and unpack, warm start, solve with prune on idle time, batched, backward) on
+        # R-MAT scale 21 (CSR 0.5 GB, larger than L2), 8 sources
+        g0 = gg.rmat(gg.BASE_SEED + 21, 21, 16 << 21)
+        srcs = gg.pick_sources(gg.BASE_SEED + 21, g0, 8)
+        g = sssp.build_csr(g0.V, g0.src, g0.dst, g0.w, partitions=148)
+        del g0
+        sssp.partition(g)
+        h = sssp.layout(g)
+        keep, _ = sssp.prune(g, 0)
+        gp = sssp.compact(g, keep)
+        src_d = torch.from_numpy(srcs.view(np.int32)).cuda()
+        opts = sssp.options(delta=5)
+        s1 = sssp.Solver(h, len(srcs), opts)
+        s1.launch(src_d)
+        d0, p0 = s1.dist.clone(), s1.pred.clone()
+        w2 = h.w.clone()
+        w2[::1000] = torch.clamp(w2[::1000] // 2, min=1)
+        h2 = sssp.DeviceGraph(h.V, h.E, h.row_ptr, h.col, w2, h.wtype, h.partitions, h.eid, h.ids, h.slots)
+        tails = h.ids.long()[torch.searchsorted(h.row_ptr.long(), torch.arange(0, h.E, 1000, device="cuda"),
+                                                right=True) - 1].int()
+        s2 = sssp.Solver(h2, len(srcs), opts)
+        s2.update(d0, p0, tails)
+        s3 = sssp.Solver(gp, len(srcs), opts)
+        kp = torch.empty(max(gp.E, 1), dtype=torch.uint8, device="cuda")
+        s3.launch_prune(src_d, 0, kp)
+        for s_ in (s1, s2, s3):
+            st, _ = s_.status()
+            assert st == sssp.SSSP_OK, st
+        graphs0, sources = gg.workload_batch512(n_graphs=64)
+        b = sssp.Batch([sssp.build_csr(x.V, x.src, x.dst, x.w) for x in graphs0], sources, sssp.options(delta=8))
+        b.solve()
+        st, _ = b.status()
+        assert st == sssp.SSSP_OK, st
+        gf0, fsrcs, gup = gg.workload_rmat18_f32()
+        gf = sssp.build_csr(gf0.V, gf0.src, gf0.dst, gf0.w, partitions=16)
+        _, fpred, st, _ = sssp.solve(gf, fsrcs)
+        gr = sssp.backward(gf, fpred, torch.from_numpy(gup).cuda())
+        torch.cuda.synchronize()
+        print("all", g.E, h.E, gp.E, float(gr.abs().sum()))
+    elif which == "batched":
         graphs0, sources = gg.workload_batch512(n_graphs=64)
         graphs = [sssp.build_csr(g.V, g.src, g.dst, g.w) for g in graphs0]
         b = sssp.Batch(graphs, sources)

@@ -98,10 +98,37 @@ typedef struct {
     uint64_t timeout_ns;   /* limit on a block's continuous idle wait (default 20 s); a persistent
                               kernel also stops after 3 x timeout_ns in total */
     uint32_t flags;        /* SSSP_FLAG_* */
-    uint32_t reserved;
+    uint32_t policy;       /* sssp_policy: which queued vertices a round of sssp_solve takes (default
+                              SSSP_POLICY_RELATIVE); sssp_solve_batched keeps its own fixed buckets */
+    uint32_t msg_buffer;   /* message buffering in sssp_solve (the push-out criteria Sec. VI leaves as
+                              future work): 0 = direct, every message (an improvement of a vertex
+                              owned by another unit) made visible to its owner at once; k in 1..32 =
+                              a warp holds its messages and pushes them out, with one release fence,
+                              once it holds k of them (size criterion) and at the end of every
+                              sub-round (age criterion).  Messages inside a unit are never held. */
+    uint32_t reserved;     /* must be 0 */
     void* ev_relax_begin;  /* cudaEvent_t or NULL: recorded on `stream` right before the relaxation kernel */
     void* ev_relax_end;    /* cudaEvent_t or NULL: recorded right after it (for timing that kernel alone) */
 } sssp_options;
+
+/* Frontier policies of sssp_solve: how a round picks, among its unit's queued
+ * vertices, the bucket it relaxes -- the approximation of Dijkstra's pop order
+ * inside a partition (Sec. III.C, DIJKSTRA) that trades asynchrony against
+ * wasted relaxations, as the Delta-stepping of the related work (Sec. II) does.
+ * All give the same distances and predecessors; dmin is the least distance
+ * queued in the unit when the round starts.
+ *   RELATIVE : dist < dmin + delta
+ *   FIXED    : dist < the end of the fixed bucket [k*delta, (k+1)*delta) holding dmin
+ *   NEAR_FAR : dist < the unit's split point, which moves to dmin + delta whenever
+ *              no queued vertex lies below it (near-far worklists: late messages
+ *              below the split join the current near set instead of narrowing it)
+ *   ALL      : every queued vertex (asynchronous Bellman-Ford; delta unused) */
+typedef enum {
+    SSSP_POLICY_RELATIVE = 0,
+    SSSP_POLICY_FIXED = 1,
+    SSSP_POLICY_NEAR_FAR = 2,
+    SSSP_POLICY_ALL = 3
+} sssp_policy;
 
 /* Test hook: start the pending count one above the true value so that the
  * termination count can never reach zero; the solve must then end with
@@ -118,6 +145,7 @@ typedef struct {
     uint64_t vertices;         /* vertices processed (taken from an inbox) */
     uint64_t remote_activations; /* activations of a vertex owned by another unit (messages, Alg. 3 send_msg) */
     uint64_t idle_us;          /* microseconds blocks spent waiting with no unit to process, summed over blocks */
+    uint64_t prune_chunks;     /* sssp_solve_prune: Trishla chunks run by idle blocks during the solve */
 } sssp_stats;
 
 const char* sssp_status_string(sssp_status s);
@@ -223,6 +251,7 @@ size_t sssp_solve_workspace_size(const sssp_graph* g, uint32_t S, const sssp_opt
  *   dist    : device [S][V] out, uint32 or float32 per g->wtype
  *   pred    : device [S][V] out (may be NULL), canonical predecessor vertex
  *   ws      : device workspace >= sssp_solve_workspace_size(g, S, opt)
+ * opt->policy chooses the frontier policy of a round (sssp_policy).
  * Launches an init kernel, one persistent cooperative relaxation kernel in
  * which each block owns (source, partition sub-block) units, and an unpack
  * kernel.  Needs every block co-resident; returns SSSP_EUNSUPPORTED if the
@@ -231,6 +260,24 @@ size_t sssp_solve_workspace_size(const sssp_graph* g, uint32_t S, const sssp_opt
  */
 sssp_status sssp_solve(const sssp_graph* g, const uint32_t* sources, uint32_t S, void* dist, uint32_t* pred,
                        const sssp_options* opt, void* ws, size_t ws_bytes, sssp_stream_t stream);
+
+/*
+ * sssp_solve and sssp_prune in one pass, with the prune run on the solve's idle
+ * time: Sec. III.B observes that a process that receives no message sits idle,
+ * and spends that time finding edges that lie on no shortest path (Trishla,
+ * Algorithm 1).  Here a block of the persistent solve that finds none of its
+ * units queued runs Trishla chunks of g instead of waiting, and goes back to its
+ * units after each chunk; the chunks left when the solve ends run in a launch
+ * right after it.  The solve reads the unpruned g (pruned edges are never on a
+ * shortest path, so its result is the same either way); the keep mask serves
+ * later solves on the compacted graph (sssp_compact).
+ *   g, sources, S, dist, pred, opt, ws, ws_bytes : as for sssp_solve
+ *   mode, keep, witness : as for sssp_prune (keep device [E], witness device [E] or NULL);
+ *                         the same values sssp_prune gives, on the CSR as stored
+ */
+sssp_status sssp_solve_prune(const sssp_graph* g, const uint32_t* sources, uint32_t S, void* dist, uint32_t* pred,
+                             int32_t mode, uint8_t* keep, uint32_t* witness, const sssp_options* opt, void* ws,
+                             size_t ws_bytes, sssp_stream_t stream);
 
 /*
  * Warm start (incremental SSSP; the paper has no such call): sssp_solve's result
@@ -257,11 +304,12 @@ sssp_status sssp_update(const sssp_graph* g, uint32_t S, void* dist, uint32_t* p
 /*
  * Autotuner for sssp_solve (the paper has no tuner; its knobs are the process
  * count and the termination timeout).  Runs sssp_solve on (g, sources) with
- * candidate schedules and returns the fastest: the bucket width delta is
- * searched over {1/64 .. 4} x the mean of a sample of the weights (powers of
- * two), refined at 3/4 and 3/2 of the best of those, then tile
- * over {1024, 2048, 4096}, then split over {1, 2, 4} (split only where ws is
- * large enough).  Each candidate runs `trials` times (>= 1) after one
+ * candidate schedules and returns the fastest: for each frontier policy
+ * RELATIVE, FIXED and NEAR_FAR the bucket width delta is searched over
+ * {1/64 .. 4} x the mean of a sample of the weights (powers of two), and ALL
+ * once; the best is refined at 3/4 and 3/2 of its delta, then tile over
+ * {1024, 2048, 4096}, then split over {1, 2, 4} (split only where ws is large
+ * enough).  The base options' policy is ignored.  Each candidate runs `trials` times (>= 1) after one
  * warm-up, timed with CUDA events on `stream`; candidates that fail are
  * skipped.  Synchronous.  Results do not depend on the schedule, so dist and
  * pred hold a valid solve afterwards.
@@ -308,6 +356,28 @@ sssp_status sssp_workspace_status(const void* ws, sssp_stream_t stream, sssp_sta
  */
 sssp_status sssp_solve_noalloc(const sssp_graph* g, const uint32_t* sources, uint32_t S, void* dist, uint32_t* pred,
                                const sssp_options* opt, uint32_t* status_out, sssp_stream_t stream);
+
+/* ------------------------------------------------------- multi-GPU sharding */
+
+/*
+ * Host-only (no device work, no stream): split independent problems across
+ * n_ranks processes, one per GPU, by their estimated cost.  The paper's only
+ * parallel strategy is the domain split over processes (Sec. III.A); for
+ * independent problems (the sources of a multi-source solve, the (graph,
+ * source) problems of a batch) the split needs no exchange at all, so each
+ * rank calls this with the same arguments, gets the same answer and solves
+ * its own problems.  Longest-processing-time-first: problems in decreasing
+ * cost (ties by index) each go to the rank with the least total cost so far
+ * (ties by lowest rank).  The largest total is then at most (4/3 - 1/(3 n_ranks))
+ * times the best possible, and at most the mean total plus the largest cost.
+ *   cost    : host [n_problems] estimated cost of each problem (for example the
+ *             edges of its graph: a solve scans every edge it reaches)
+ *   rank_of : host [n_problems] out, the rank (< n_ranks) that solves each problem
+ *   load    : host [n_ranks] out (may be NULL), total cost given to each rank
+ * Returns SSSP_EINVAL for n_ranks == 0 or NULL arrays (with n_problems > 0).
+ */
+sssp_status sssp_shard_problems(uint32_t n_problems, const uint64_t* cost, uint32_t n_ranks, uint32_t* rank_of,
+                                uint64_t* load);
 
 /* ------------------------------------------------------------ K5 batched */
 

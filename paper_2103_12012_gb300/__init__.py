@@ -22,6 +22,8 @@ _lib = None
 SSSP_OK, SSSP_EINVAL, SSSP_ENOMEM, SSSP_ECUDA, SSSP_ETIMEOUT, SSSP_EOVERFLOW, SSSP_EINTERNAL, SSSP_EUNSUPPORTED = \
     range(8)
 W_U32, W_F32 = 0, 1
+POLICY_RELATIVE, POLICY_FIXED, POLICY_NEAR_FAR, POLICY_ALL = range(4)
+POLICY_NAMES = ("relative", "fixed", "near_far", "all")
 FLAG_TEST_HOLD_PENDING = 0x1
 NONE = 0xFFFFFFFF
 
@@ -36,13 +38,14 @@ class SsspGraph(ctypes.Structure):
 
 class SsspOptions(ctypes.Structure):
     _fields_ = [("threads", u32), ("blocks_per_sm", u32), ("tile", u32), ("split", u32),
-                ("delta", ctypes.c_double), ("timeout_ns", u64), ("flags", u32), ("reserved", u32),
-                ("ev_relax_begin", P), ("ev_relax_end", P)]
+                ("delta", ctypes.c_double), ("timeout_ns", u64), ("flags", u32), ("policy", u32),
+                ("msg_buffer", u32), ("reserved", u32), ("ev_relax_begin", P), ("ev_relax_end", P)]
 
 
 class SsspStats(ctypes.Structure):
     _fields_ = [("edges_scanned", u64), ("atomics", u64), ("improved", u64), ("activations", u64),
-                ("rounds", u64), ("vertices", u64), ("remote_activations", u64), ("idle_us", u64)]
+                ("rounds", u64), ("vertices", u64), ("remote_activations", u64), ("idle_us", u64),
+                ("prune_chunks", u64)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -82,6 +85,8 @@ _SIGS = {
     "sssp_batch_plan_destroy": (None, [P]),
     "sssp_backward_workspace_size": (sz, [u32, u32, u32]),
     "sssp_backward": (i32, [P, u32, P, P, P, P, sz, P]),
+    "sssp_shard_problems": (i32, [u32, P, u32, P, P]),
+    "sssp_solve_prune": (i32, [P, P, u32, P, P, i32, P, P, P, P, sz, P]),
 }
 
 
@@ -137,8 +142,10 @@ def _ws(nbytes):
     return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device="cuda")
 
 
-def options(threads=0, blocks_per_sm=0, tile=0, split=0, delta=0.0, timeout_ns=0, flags=0) -> SsspOptions:
-    return SsspOptions(threads, blocks_per_sm, tile, split, float(delta), int(timeout_ns), flags, 0, None, None)
+def options(threads=0, blocks_per_sm=0, tile=0, split=0, delta=0.0, timeout_ns=0, flags=0,
+            policy=POLICY_RELATIVE, msg_buffer=0) -> SsspOptions:
+    return SsspOptions(threads, blocks_per_sm, tile, split, float(delta), int(timeout_ns), flags, int(policy),
+                       int(msg_buffer), 0, None, None)
 
 
 @dataclass
@@ -301,6 +308,17 @@ class Solver:
         _check(st, "sssp_solve")
         return dist, pred
 
+    def launch_prune(self, sources, mode, keep, witness=None, dist=None, pred=None, stream=None):
+        """sssp_solve_prune, asynchronous: the solve of launch(), with Trishla (mode 0 local, 1 global)
+        run on the solve's idle time into keep (uint8 [E]) and witness (int32 [E] or None)."""
+        dist = self.dist if dist is None else dist
+        pred = self.pred if pred is None else pred
+        st = lib().sssp_solve_prune(ctypes.byref(self.gc), _ptr(sources), self.S, _ptr(dist), _ptr(pred), int(mode),
+                                    _ptr(keep), _ptr(witness), ctypes.byref(self.opts), _ptr(self.ws), self.ws_bytes,
+                                    _stream(stream))
+        _check(st, "sssp_solve_prune")
+        return dist, pred
+
     def update(self, dist, pred, tails, stream=None):
         """sssp_update (warm start), asynchronous: dist/pred hold a result for this solver's S
         sources on the graph before some weights fell or edges were added; they are updated in
@@ -355,9 +373,10 @@ def autotune(g: DeviceGraph, sources, base: SsspOptions | None = None, trials: i
                 db = json.load(f)
         except ValueError:
             db = {}
-    if key in db:
+    if key in db and "policy" in db[key]:
         o = db[key]
-        return options(threads=o["threads"], tile=o["tile"], split=o["split"], delta=o["delta"]), None
+        return options(threads=o["threads"], tile=o["tile"], split=o["split"], delta=o["delta"],
+                       policy=o["policy"]), None
     solver = Solver(g, S, options(split=4))  # workspace large enough for every split candidate
     if isinstance(sources, np.ndarray) or isinstance(sources, (list, tuple)):
         sources = _as_dev_u32(np.asarray(sources, np.uint32))
@@ -368,7 +387,7 @@ def autotune(g: DeviceGraph, sources, base: SsspOptions | None = None, trials: i
                                _ptr(solver.ws), solver.ws_bytes, ctypes.byref(b), trials, ctypes.byref(best),
                                ctypes.byref(ms), _stream()), "sssp_autotune")
     rec = dict(threads=int(best.threads), tile=int(best.tile), split=int(best.split), delta=float(best.delta),
-               ms=round(float(ms.value), 4))
+               policy=int(best.policy), ms=round(float(ms.value), 4))
     if cache:
         db[key] = rec
         os.makedirs(os.path.dirname(path), exist_ok=True)
@@ -376,7 +395,8 @@ def autotune(g: DeviceGraph, sources, base: SsspOptions | None = None, trials: i
         with open(tmp, "w") as f:
             json.dump(db, f, indent=1, sort_keys=True)
         os.replace(tmp, path)
-    return options(threads=rec["threads"], tile=rec["tile"], split=rec["split"], delta=rec["delta"]), rec["ms"]
+    return options(threads=rec["threads"], tile=rec["tile"], split=rec["split"], delta=rec["delta"],
+                   policy=rec["policy"]), rec["ms"]
 
 
 def solve(g: DeviceGraph, sources, opts: SsspOptions | None = None, check=True):
@@ -384,6 +404,23 @@ def solve(g: DeviceGraph, sources, opts: SsspOptions | None = None, check=True):
     s = Solver(g, len(sources) if not hasattr(sources, "numel") else sources.numel(), opts)
     d, p = s(sources, check=check)
     return d.clone(), p.clone(), s.last_status, s.last_stats
+
+
+def solve_prune(g: DeviceGraph, sources, mode=0, opts: SsspOptions | None = None, witness=True, check=True):
+    """sssp_solve_prune: (dist, pred, keep, witness or None, status, stats) -- the solve, with
+    Trishla on g run by the solve's idle blocks (and finished right after it)."""
+    torch = _torch()
+    S = len(sources) if not hasattr(sources, "numel") else int(sources.numel())
+    s = Solver(g, S, opts)
+    if isinstance(sources, np.ndarray) or isinstance(sources, (list, tuple)):
+        sources = _as_dev_u32(np.asarray(sources, np.uint32))
+    keep = torch.empty(max(g.E, 1), dtype=torch.uint8, device="cuda")
+    wit = torch.empty(max(g.E, 1), dtype=torch.int32, device="cuda") if witness else None
+    s.launch_prune(sources, mode, keep, wit)
+    st, stats = s.status()
+    if check and st != SSSP_OK:
+        raise SsspError(st, "sssp_solve_prune (device)")
+    return s.dist.clone(), s.pred.clone(), keep[:g.E], (wit[:g.E] if wit is not None else None), st, stats
 
 
 def update(g: DeviceGraph, dist, pred, tails, opts: SsspOptions | None = None, check=True):
@@ -527,6 +564,66 @@ class Batch:
         if getattr(self, "plan", None) is not None and _lib is not None:
             _lib.sssp_batch_plan_destroy(self.plan)
             self.plan = None
+
+
+def shard_problems(costs, world: int):
+    """sssp_shard_problems (host only): (rank of each problem, total cost of each rank) for
+    independent problems with the given estimated costs, split over `world` ranks."""
+    costs = np.ascontiguousarray(np.asarray(costs, np.uint64))
+    rank_of = np.empty(max(costs.size, 1), np.uint32)
+    load = np.empty(max(int(world), 1), np.uint64)
+    _check(lib().sssp_shard_problems(costs.size, costs.ctypes.data, int(world), rank_of.ctypes.data,
+                                     load.ctypes.data), "sssp_shard_problems")
+    return rank_of[:costs.size], load[:int(world)]
+
+
+def shard_batch(graphs, sources, rank: int, world: int):
+    """The (graph, source) problems of a batch that `rank` of `world` solves, split by estimated
+    cost (the edges of the problem's graph, plus its vertices).  graphs: objects with V and E
+    (or E_raw, or a canonical row_ptr); sources: one array per graph.  Returns (graph indices, sources
+    per kept graph), ready for Batch; every rank computes the same split, with no exchange."""
+    sizes = []
+    for g in graphs:
+        if hasattr(g, "E"):
+            E = int(g.E)
+        elif hasattr(g, "E_raw"):  # an edge list not yet made canonical: its raw edges
+            E = int(g.E_raw)
+        else:
+            E = int(np.asarray(g.row_ptr)[-1])
+        sizes.append(E + int(g.V))
+    costs, owner = [], []
+    for gi, s in enumerate(sources):
+        for _ in np.asarray(s).tolist():
+            costs.append(sizes[gi])
+            owner.append(gi)
+    rank_of, _ = shard_problems(costs, world)
+    keep_g, keep_s = [], []
+    k = 0
+    for gi, s in enumerate(sources):
+        s = np.asarray(s)
+        mine = s[rank_of[k:k + s.size] == rank]
+        k += s.size
+        if mine.size:
+            keep_g.append(gi)
+            keep_s.append(mine.astype(np.uint32))
+    return keep_g, keep_s
+
+
+def shard_sources(n_sources: int, rank: int, world: int):
+    """Indices of the sources of one multi-source solve that `rank` of `world` solves (equal
+    costs: the planner deals them out in turn)."""
+    rank_of, _ = shard_problems(np.ones(n_sources, np.uint64), world)
+    return np.nonzero(rank_of == rank)[0]
+
+
+def allreduce_sum(t):
+    """Sum a tensor over the ranks of the default torch.distributed group (in place; no-op with
+    one rank): the single exchange of the sharded differentiable form, dL/dw summed over the
+    ranks' sources."""
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return t
 
 
 def backward(g: DeviceGraph, pred, grad_dist, stream=None):

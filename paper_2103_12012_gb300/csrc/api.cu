@@ -25,7 +25,7 @@ constexpr float DEF_DELTA_F32 = 0.0625f;
 
 struct Resolved {
     uint32_t threads, tile, split, bps;
-    uint32_t delta_bits;
+    uint32_t delta_bits, policy, msg_buffer;
     uint64_t timeout_ns;
     uint32_t flags;
     cudaEvent_t ev_begin, ev_end;
@@ -60,18 +60,22 @@ bool resolve(const sssp_options* o, int wtype, Resolved* r) {
     r->delta_bits = delta_bits_for(wtype, o->delta);
     r->timeout_ns = o->timeout_ns ? o->timeout_ns : DEF_TIMEOUT_NS;
     r->flags = o->flags;
+    r->policy = o->policy;
+    r->msg_buffer = o->msg_buffer;
     r->ev_begin = static_cast<cudaEvent_t>(o->ev_relax_begin);
     r->ev_end = static_cast<cudaEvent_t>(o->ev_relax_end);
     if (r->threads < 128 || r->threads > 1024 || (r->threads % 32)) return false;
     if (r->tile < 32 || r->tile > 4096) return false;
     if (r->split > 1024) return false;
+    if (r->policy > SSSP_POLICY_ALL) return false;
+    if (r->msg_buffer > 32 || o->reserved != 0) return false;
     if (!(o->delta >= 0.0) || std::isinf(o->delta)) return false;
     return true;
 }
 
-// Workspace of sssp_solve: header | packed[S][V] | bitmap[S][words] | dirty[S*Q]
+// Workspace of sssp_solve: header | packed[S][V] | bitmap[S][words] | dirty[S*Q] | nfsplit[S*Q]
 struct SolveWs {
-    size_t off_packed, off_bitmap, off_dirty, total;
+    size_t off_packed, off_bitmap, off_dirty, off_nf, total;
     uint32_t words, B, Bq, Q;
 };
 
@@ -87,6 +91,8 @@ SolveWs solve_layout(const sssp_graph* g, uint32_t S, uint32_t split) {
     w.off_bitmap = off;
     off += align_up(4ull * S * w.words, 256);
     w.off_dirty = off;
+    off += align_up(4ull * S * w.Q, 256);
+    w.off_nf = off;
     off += align_up(4ull * S * w.Q, 256);
     w.total = off;
     return w;
@@ -177,7 +183,8 @@ size_t sssp_solve_workspace_size(const sssp_graph* g, uint32_t S, const sssp_opt
 // sssp_solve (sources given) and sssp_update (warm: from the result in dist/pred)
 static sssp_status solve_impl(const sssp_graph* g, const uint32_t* sources, uint32_t S, void* dist, uint32_t* pred,
                               const sssp_options* opt, void* ws, size_t ws_bytes, sssp_stream_t stream,
-                              const uint32_t* tails, uint32_t n_tails, bool warm) {
+                              const uint32_t* tails, uint32_t n_tails, bool warm, int prune_mode = -1,
+                              uint8_t* keep = nullptr, uint32_t* witness = nullptr) {
     Resolved r;
     if (!graph_ok(g) || S == 0 || (!warm && !sources) || !dist || !ws || !resolve(opt, g->wtype, &r))
         return SSSP_EINVAL;
@@ -185,10 +192,12 @@ static sssp_status solve_impl(const sssp_graph* g, const uint32_t* sources, uint
     const SolveWs L = solve_layout(g, S, r.split);
     if ((uint64_t)S * L.Q > 0xFFFFFFFFull / 2 || L.Q > MAX_UNITS_PER_SOURCE * 16u) return SSSP_EINVAL;
     if (ws_bytes < L.total) return SSSP_ENOMEM;
-    const size_t smem = relax_smem_bytes(r.tile, L.Q);
+    const size_t smem = relax_smem_bytes(r.tile, L.Q, r.msg_buffer != 0);
     if (smem > 200 * 1024) return SSSP_EINVAL;
+    const bool prune = prune_mode >= 0;
     int per_sm = 0;
-    if (relax_max_blocks_per_sm(g->wtype, r.threads, r.tile, L.Q, &per_sm) != cudaSuccess) return SSSP_ECUDA;
+    if (relax_max_blocks_per_sm(g->wtype, r.threads, r.tile, L.Q, &per_sm, prune, r.msg_buffer != 0) != cudaSuccess)
+        return SSSP_ECUDA;
     if (per_sm <= 0) return SSSP_EUNSUPPORTED;
     if (r.bps) per_sm = std::min<int>(per_sm, (int)r.bps);
     const uint64_t U = (uint64_t)S * L.Q;
@@ -212,10 +221,13 @@ static sssp_status solve_impl(const sssp_graph* g, const uint32_t* sources, uint
     l.packed = reinterpret_cast<unsigned long long*>(base + L.off_packed);
     l.bitmap = reinterpret_cast<uint32_t*>(base + L.off_bitmap);
     l.dirty = reinterpret_cast<uint32_t*>(base + L.off_dirty);
+    l.nfsplit = reinterpret_cast<uint32_t*>(base + L.off_nf);
     l.threads = r.threads;
     l.tile = r.tile;
     l.grid = (uint32_t)std::min<uint64_t>(U, (uint64_t)per_sm * sm_count());
     l.delta_bits = r.delta_bits;
+    l.policy = r.policy;
+    l.msg_buffer = r.msg_buffer;
     l.timeout_ns = r.timeout_ns;
     l.hold_pending = (r.flags & SSSP_FLAG_TEST_HOLD_PENDING) ? 1u : 0u;
     l.ev_begin = r.ev_begin;
@@ -225,12 +237,21 @@ static sssp_status solve_impl(const sssp_graph* g, const uint32_t* sources, uint
     l.warm = warm ? 1u : 0u;
     l.warm_tails = tails;
     l.n_tails = n_tails;
+    l.prune_on = prune ? 1u : 0u;
+    if (prune) l.prune = trishla_job(g, prune_mode, keep, witness);
     return launch_solve(l, (cudaStream_t)stream) == cudaSuccess ? SSSP_OK : SSSP_ECUDA;
 }
 
 sssp_status sssp_solve(const sssp_graph* g, const uint32_t* sources, uint32_t S, void* dist, uint32_t* pred,
                        const sssp_options* opt, void* ws, size_t ws_bytes, sssp_stream_t stream) {
     return solve_impl(g, sources, S, dist, pred, opt, ws, ws_bytes, stream, nullptr, 0, false);
+}
+
+sssp_status sssp_solve_prune(const sssp_graph* g, const uint32_t* sources, uint32_t S, void* dist, uint32_t* pred,
+                             int32_t mode, uint8_t* keep, uint32_t* witness, const sssp_options* opt, void* ws,
+                             size_t ws_bytes, sssp_stream_t stream) {
+    if ((mode != 0 && mode != 1) || (g && g->E && !keep)) return SSSP_EINVAL;
+    return solve_impl(g, sources, S, dist, pred, opt, ws, ws_bytes, stream, nullptr, 0, false, mode, keep, witness);
 }
 
 sssp_status sssp_update(const sssp_graph* g, uint32_t S, void* dist, uint32_t* pred, const uint32_t* tails,
@@ -297,13 +318,18 @@ sssp_status sssp_autotune(const sssp_graph* g, const uint32_t* sources, uint32_t
     sssp_options cur = b;
     float cur_ms = INFINITY;
     const double factors[] = {1.0 / 64, 1.0 / 32, 1.0 / 16, 1.0 / 8, 1.0 / 4, 1.0 / 2, 1.0, 2.0, 4.0};
-    for (double f : factors) {
-        sssp_options o = b;
-        o.delta = g->wtype == SSSP_W_F32 ? mean * f : std::max(1.0, std::floor(mean * f));
-        const float ms = run(o);
-        if (ms < cur_ms) {
-            cur_ms = ms;
-            cur = o;
+    for (uint32_t pol : {(uint32_t)SSSP_POLICY_RELATIVE, (uint32_t)SSSP_POLICY_FIXED, (uint32_t)SSSP_POLICY_NEAR_FAR,
+                         (uint32_t)SSSP_POLICY_ALL}) {
+        for (double f : factors) {
+            sssp_options o = b;
+            o.policy = pol;
+            o.delta = g->wtype == SSSP_W_F32 ? mean * f : std::max(1.0, std::floor(mean * f));
+            const float ms = run(o);
+            if (ms < cur_ms) {
+                cur_ms = ms;
+                cur = o;
+            }
+            if (pol == SSSP_POLICY_ALL) break;  // delta unused
         }
     }
     // refine the bucket width between the coarse steps
@@ -352,10 +378,36 @@ sssp_status sssp_workspace_status(const void* ws, sssp_stream_t stream, sssp_sta
     WsHeader h;
     if (cudaMemcpy(&h, ws, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return SSSP_ECUDA;
     if (stats) {
-        static_assert(sizeof(sssp_stats) == 8 * sizeof(uint64_t), "stats layout");
+        static_assert(sizeof(sssp_stats) == 9 * sizeof(uint64_t), "stats layout");
         std::memcpy(stats, h.stats, sizeof(sssp_stats));
     }
     return (sssp_status)h.status;
+}
+
+// ------------------------------------------------------------------ sharding
+
+sssp_status sssp_shard_problems(uint32_t n_problems, const uint64_t* cost, uint32_t n_ranks, uint32_t* rank_of,
+                                uint64_t* load) {
+    if (n_ranks == 0 || (n_problems && (!cost || !rank_of))) return SSSP_EINVAL;
+    std::vector<uint32_t> order(n_problems);
+    std::iota(order.begin(), order.end(), 0u);
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return cost[a] > cost[b]; });
+    // min-heap of (load, rank): the least loaded rank, lowest rank on ties
+    std::vector<std::pair<uint64_t, uint32_t>> heap(n_ranks);
+    for (uint32_t r = 0; r < n_ranks; ++r) heap[r] = {0ull, r};
+    auto greater = [](const std::pair<uint64_t, uint32_t>& x, const std::pair<uint64_t, uint32_t>& y) {
+        return x > y;
+    };
+    std::make_heap(heap.begin(), heap.end(), greater);
+    for (uint32_t i : order) {
+        std::pop_heap(heap.begin(), heap.end(), greater);
+        rank_of[i] = heap.back().second;
+        heap.back().first += cost[i];
+        std::push_heap(heap.begin(), heap.end(), greater);
+    }
+    if (load)
+        for (const auto& h : heap) load[h.second] = h.first;
+    return SSSP_OK;
 }
 
 // ------------------------------------------------------------------ batched

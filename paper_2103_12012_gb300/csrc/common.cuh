@@ -19,8 +19,8 @@ struct WsHeader {
     uint32_t abort_flag;    // set on a fatal device error so every block stops
     unsigned long long pending;  // queued-but-unprocessed vertices (Sec. III.D counter)
     unsigned long long work_next;  // batched work-queue cursor
-    unsigned long long stats[8];   // sssp_stats
-    uint32_t pad[(256 - 4 - 4 - 8 - 8 - 64) / 4];
+    unsigned long long stats[9];   // sssp_stats
+    uint32_t pad[(256 - 4 - 4 - 8 - 8 - 72) / 4];
 };
 static_assert(sizeof(WsHeader) == 256, "header size");
 
@@ -72,6 +72,12 @@ struct WU32 {
     __device__ __forceinline__ static uint32_t inf_out() { return INF32; }
     // index of the width-delta distance bucket of d (delta >= 1); non-decreasing in d
     __device__ __forceinline__ static uint32_t bucket(uint32_t d, uint32_t delta) { return d / delta; }
+    // end of the fixed bucket [k*delta, (k+1)*delta) that holds d: above d, non-decreasing in d,
+    // saturating to 0xFFFFFFFF (every finite distance)
+    __device__ __forceinline__ static uint32_t bucket_end(uint32_t d, uint32_t delta) {
+        const unsigned long long e = ((unsigned long long)(d / delta) + 1ull) * delta;
+        return e < 0xFFFFFFFFull ? (uint32_t)e : 0xFFFFFFFFu;
+    }
 };
 
 struct WF32 {
@@ -89,6 +95,14 @@ struct WF32 {
     __device__ __forceinline__ static uint32_t bucket(uint32_t d, uint32_t delta_bits) {
         const float q = __fdiv_rn(__uint_as_float(d), __uint_as_float(delta_bits));
         return q < 4.0e9f ? (uint32_t)q : 4000000000u;
+    }
+    // end of the fixed bucket that holds d: (floor(d / delta) + 1) * delta, each step rounded
+    // once (monotone), and at least one step above d (bit patterns, numeric order)
+    __device__ __forceinline__ static uint32_t bucket_end(uint32_t d, uint32_t delta_bits) {
+        const float dl = __uint_as_float(delta_bits);
+        const float q = floorf(__fdiv_rn(__uint_as_float(d), dl));
+        const uint32_t e = __float_as_uint(__fmul_rn(__fadd_rn(q, 1.0f), dl));
+        return e > d ? e : d + 1u;
     }
 };
 

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include "sssp.h"
+#include "trishla.cuh"
 
 namespace sssp {
 
@@ -35,9 +36,12 @@ struct SolveLaunch {
     unsigned long long* packed;  // [S][V]
     uint32_t* bitmap;            // [S][words]
     uint32_t* dirty;             // [S*Q]
+    uint32_t* nfsplit;           // [S*Q] near-far split point per unit
     // schedule
     uint32_t threads, tile, grid;
     uint32_t delta_bits;
+    uint32_t policy;      // SSSP_POLICY_*
+    uint32_t msg_buffer;  // 0: direct messages, else the push-out size
     uint64_t timeout_ns;
     uint32_t hold_pending;
     cudaEvent_t ev_begin, ev_end;  // optional timing events around the relaxation kernel
@@ -48,11 +52,15 @@ struct SolveLaunch {
     uint32_t warm;
     const uint32_t* warm_tails;
     uint32_t n_tails;
+    // prune while idle (sssp_solve_prune): blocks with no dirty unit run Trishla chunks
+    uint32_t prune_on;
+    TrishlaJob prune;
 };
 
 constexpr uint32_t SOLVE_MAX_THREADS = 512;  // block size limit of the solve kernel
-size_t relax_smem_bytes(uint32_t tile, uint32_t Q);
-cudaError_t relax_max_blocks_per_sm(int wtype, uint32_t threads, uint32_t tile, uint32_t Q, int* out);
+size_t relax_smem_bytes(uint32_t tile, uint32_t Q, bool msgs);
+cudaError_t relax_max_blocks_per_sm(int wtype, uint32_t threads, uint32_t tile, uint32_t Q, int* out,
+                                    bool prune = false, bool msgs = false);
 cudaError_t launch_solve(const SolveLaunch& L, cudaStream_t st);
 
 // One problem of a batch, in the order blocks take them (largest first).
@@ -101,6 +109,11 @@ sssp_status compact_launch(const sssp_graph* g, const uint8_t* keep, uint32_t* r
 
 // ------------------------------------------------------------------ prune.cu
 cudaError_t prune_launch(const sssp_graph* g, int mode, uint8_t* keep, uint32_t* witness, cudaStream_t st);
+TrishlaJob trishla_job(const sssp_graph* g, int mode, uint8_t* keep, uint32_t* witness);
+cudaError_t trishla_init(const TrishlaJob& J, cudaStream_t st);  // keep = 1, witness = NONE
+// every pair of every chunk (cursor NULL), or what a solve's idle blocks left of the job: the
+// heavy pairs of the chunks below *cursor and every pair of the others
+cudaError_t trishla_launch(const TrishlaJob& J, int wtype, const unsigned long long* cursor, cudaStream_t st);
 
 // --------------------------------------------------------------- backward.cu
 size_t backward_workspace_bytes(uint32_t V, uint32_t E, uint32_t S);

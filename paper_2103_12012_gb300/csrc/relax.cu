@@ -61,10 +61,12 @@ constexpr uint32_t MAX_SUBROUNDS = 256;       // local sub-rounds one round may 
 constexpr uint32_t GATHER_MIN = 1024;          // queued vertices one scan can keep (at least)
 constexpr int GATHER_G = 2;                   // queued vertices a lane enumerates and loads together
 constexpr uint32_t IDLE_BACKOFF_MAX_NS = 1024;  // longest sleep of a block with no dirty unit
+constexpr uint64_t PRUNE_IDLE_NS = 20000;      // idle this long before a block runs Trishla chunks
 // batched distance buckets: BK_NB fine buckets of width delta (the current coarse bucket),
 // BK_NC coarse buckets of width BK_NB * delta after it, then one overflow
 constexpr uint32_t BK_NB = 16, BK_NC = 16, BK_OV = BK_NB + BK_NC, BK_SLOTS = BK_NB + BK_NC + 1;
 constexpr int EDGE_BATCH = 3;                // edges in flight per thread in phase E (measured: 2-4 similar)
+constexpr uint32_t MSG_CAP = 64;             // messages one warp can hold (msg_buffer <= 32, plus one batch of 32)
 // Termination counts a round reserves before any of its inbox bits can be visible.  A round
 // runs at most MAX_SUBROUNDS sub-rounds; a sub-round relaxes the edges of distinct vertices,
 // fewer than 2^32 (E is 32-bit), and turns on at most one inbox bit per relaxed edge, so a
@@ -191,8 +193,27 @@ __device__ __forceinline__ uint32_t bucket_bound(uint32_t dmin, uint32_t delta) 
     return t > dmin ? t : dmin + 1u;
 }
 
+// Bound of a round's bucket under the chosen frontier policy (every policy gives the same
+// result; they differ in how many vertices a round takes).  Non-decreasing in dmin and above
+// it, so a bound computed from a running minimum is never below the final one.
+//   RELATIVE   dmin + delta
+//   FIXED      the end of the fixed width-delta bucket holding dmin (Delta-stepping's buckets)
+//   NEAR_FAR   the unit's split point nf while dmin lies below it, else dmin + delta (the round
+//              then moves the split there)
+//   ALL        every queued vertex (asynchronous Bellman-Ford inside the partition)
+template <class W>
+__device__ __forceinline__ uint32_t policy_bound(uint32_t dmin, uint32_t delta, uint32_t policy, uint32_t nf) {
+    switch (policy) {
+        case SSSP_POLICY_FIXED: return W::bucket_end(dmin, delta);
+        case SSSP_POLICY_NEAR_FAR: return dmin < nf ? nf : bucket_bound<W>(dmin, delta);
+        case SSSP_POLICY_ALL: return 0xFFFFFFFFu;
+        default: return bucket_bound<W>(dmin, delta);
+    }
+}
+
 struct Scalars {
     uint32_t cnt, nlist, dmin, nsel, nclaim, bad, te;
+    uint32_t nf;  // near-far policy: this unit's split point at the start of the round
     unsigned long long act;  // inbox bits this round turned on (64-bit: see ROUND_RESERVE)
     uint32_t nlq[2];  // local-queue counts of even and odd sub-rounds (a small sub-round ends
                       // without the barrier after which one counter could be reset for the next)
@@ -205,11 +226,13 @@ struct Scalars {
     // thread 0's scheduling state (static mode), here rather than in every thread's registers
     uint32_t backoff;
     unsigned long long idle_start, t_begin;
+    uint32_t prune_done;  // prune while idle: the job's chunks have all been handed out
+    uint32_t prune_go;    // prune while idle: this pass runs a chunk (set by the pick)
 };
 
 // Block statistics in shared memory, in sssp_stats order (idle time in ns until
 // the flush): kept there rather than in registers every thread would carry.
-enum : int { ST_EDGES, ST_ATOMICS, ST_IMPROVED, ST_ACTS, ST_ROUNDS, ST_VERTS, ST_REMOTE, ST_IDLE, ST_N };
+enum : int { ST_EDGES, ST_ATOMICS, ST_IMPROVED, ST_ACTS, ST_ROUNDS, ST_VERTS, ST_REMOTE, ST_IDLE, ST_PRUNE, ST_N };
 
 // Per-round view of one problem (one source on one graph).
 struct Ctx {
@@ -222,8 +245,11 @@ struct Ctx {
     uint32_t* bitmap;
     WsHeader* hdr;
     uint32_t delta, tile, gcap;
+    uint32_t policy;  // SSSP_POLICY_* (static mode; the batched kernel has its own buckets)
+    uint32_t msg_buffer;  // 0: direct messages; k: a warp pushes its held messages out at k (static mode)
     // static-ownership mode only
     uint32_t* dirty;  // this source's unit doorbells
+    uint32_t* nf;     // this source's near-far split point per unit (owner block only)
     uint32_t B, Bq, split, Qw;
     uint32_t words;  // batched buckets: inbox words of one bucket bitmap
 };
@@ -235,6 +261,7 @@ struct Smem {
     uint32_t* sel_pref; // [tile+1] degree prefix sums
     uint32_t* lq;       // [tile]  vertices of this unit lowered below the bucket bound (next sub-round)
     uint32_t* touched;  // [Qw] units that got a new queued vertex this round (static mode)
+    uint32_t* msg;      // [warps][MSG_CAP] held messages (message buffering only, else NULL)
     uint32_t* wsum;     // [32]
     Scalars* sc;
     unsigned long long* st;  // [ST_N] block statistics
@@ -274,10 +301,11 @@ __device__ __forceinline__ void bucket_file(const Ctx& c, uint32_t v, uint32_t d
 
 // One round over the unit owning vertices [lo, hi).  Returns the number of
 // queued vertices the scan found (0 = the unit's inbox was empty).
-template <class W, bool STATIC, bool BK>
+template <class W, bool STATIC, bool BK, bool HELD = false>
 __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t my_q,
                                 const Smem& sm) {
     static_assert(!(STATIC && BK), "distance buckets belong to the batched kernel");
+    static_assert(!HELD || STATIC, "message buffering belongs to the persistent solve");
     const uint32_t T = blockDim.x, tid = threadIdx.x, lane = tid & 31u;
     Scalars& sc = *sm.sc;
     if (tid == 0) {
@@ -288,6 +316,7 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
         sc.nclaim = 0;
         sc.act = 0;
         sc.bad = 0;
+        if (STATIC) sc.nf = c.policy == SSSP_POLICY_NEAR_FAR ? c.nf[my_q] : 0u;
         // (static mode: the pick reserved this round's termination counts)
     }
     __syncthreads();
@@ -483,7 +512,8 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
                 }
                 bm = warp_min(bm);  // lane 0's first element is valid: bm is a distance
                 if (lane == 0) atomicMin(&sc.dmin, bm);
-                const uint32_t bound = bucket_bound<W>(min(bm, *(volatile uint32_t*)&sc.dmin), c.delta);
+                const uint32_t bound =
+                    policy_bound<W>(min(bm, *(volatile uint32_t*)&sc.dmin), c.delta, c.policy, sc.nf);
 #pragma unroll
                 for (int g = 0; g < GATHER_G; ++g) {
                     const uint32_t k = warp_slot(ds[g] < bound, &sc.nlist, lane);
@@ -497,7 +527,9 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
         __syncthreads();
         found = sc.cnt;
         if (found != 0) {
-            thr = bucket_bound<W>(sc.dmin, c.delta);
+            thr = policy_bound<W>(sc.dmin, c.delta, c.policy, sc.nf);
+            // near-far: the near set ran dry below the split, so the split moves up
+            if (STATIC && tid == 0 && c.policy == SSSP_POLICY_NEAR_FAR && sc.dmin >= sc.nf) c.nf[my_q] = thr;
             const uint32_t nkept = sc.nlist;
 
             // ---- B: the near bucket, at most `tile` vertices: from the kept candidates,
@@ -676,7 +708,22 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
                     }
                 }
             } else {
-                for (uint32_t k0 = consec ? tid * EDGE_BATCH : tid; k0 < te; k0 += EDGE_BATCH * T) {
+                // message buffering: this warp's held messages (count warp-uniform)
+                constexpr bool held = HELD;
+                uint32_t* const mbuf = held ? sm.msg + (tid >> 5) * MSG_CAP : nullptr;
+                uint32_t mn = 0;
+                auto push_out = [&]() {  // every lowered word of the warp, one fence, then the bits
+                    __syncwarp();
+                    __threadfence();
+                    for (uint32_t i = lane; i < mn; i += 32u) inbox_set<STATIC>(c, mbuf[i], my_q, sm, lact, n_rem);
+                    __syncwarp();
+                    mn = 0;
+                };
+                // with held messages the warp's lanes stay together (ballots): the trip count follows
+                // lane 0's first edge, and lanes past the end carry no edge
+                const uint32_t kwarp0 = consec ? (tid & ~31u) * EDGE_BATCH : (tid & ~31u);
+                for (uint32_t k0 = consec ? tid * EDGE_BATCH : tid, kw = kwarp0; (held ? kw : k0) < te;
+                     k0 += EDGE_BATCH * T, kw += EDGE_BATCH * T) {
                     uint32_t vv[EDGE_BATCH], cc[EDGE_BATCH], aa[EDGE_BATCH];
     #pragma unroll
                     for (int j = 0; j < EDGE_BATCH; ++j) aa[j] = 0;
@@ -755,6 +802,16 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
                         atomicAdd(&sm.st[ST_IMPROVED], (unsigned long long)(n_ai >> 16));
                         n_ai = 0;
                     }
+                    uint32_t msgs = 0;  // improved vertices of other units, held for a push-out
+                    if (held && improved) {
+    #pragma unroll
+                        for (int j = 0; j < EDGE_BATCH; ++j) {
+                            if (!(improved & (1u << j))) continue;
+                            const uint32_t p = vv[j] / c.B;
+                            if (p * c.split + (vv[j] - p * c.B) / c.Bq != my_q) msgs |= 1u << j;
+                        }
+                        improved &= ~msgs;
+                    }
                     if (improved) {
                         // every lowered word before any of this thread's inbox bits (release);
                         // with buckets the only reader is this block, after its barriers
@@ -769,7 +826,18 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
                                 inbox_set<STATIC>(c, v, my_q, sm, lact, n_rem);
                         }
                     }
+                    if (held) {
+    #pragma unroll
+                        for (int j = 0; j < EDGE_BATCH; ++j) {
+                            const bool has = (msgs >> j) & 1u;
+                            const uint32_t ball = __ballot_sync(0xFFFFFFFFu, has);
+                            if (has) mbuf[mn + (uint32_t)__popc(ball & ((1u << lane) - 1u))] = vv[j];
+                            mn += (uint32_t)__popc(ball);
+                            if (mn >= c.msg_buffer) push_out();  // size criterion
+                        }
+                    }
                 }
+                if (held && mn) push_out();  // age criterion: the end of the sub-round
             }
             lact = warp_sum(lact);
             bad = __reduce_or_sync(0xFFFFFFFFu, bad);
@@ -845,7 +913,7 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
 __host__ __device__ inline uint32_t gather_cap(uint32_t tile) { return tile > GATHER_MIN ? tile : GATHER_MIN; }
 
 __device__ Smem carve(uint32_t* dsm, uint32_t tile, uint32_t Qw, uint32_t* wsum, Scalars* sc,
-                      unsigned long long* st) {
+                      unsigned long long* st, bool msgs = false) {
     const uint32_t gcap = gather_cap(tile);
     Smem s;
     s.list_v = dsm;
@@ -854,6 +922,7 @@ __device__ Smem carve(uint32_t* dsm, uint32_t tile, uint32_t Qw, uint32_t* wsum,
     s.sel_pref = s.sel_v + tile;
     s.lq = s.sel_pref + tile + 1;
     s.touched = s.lq + tile;
+    s.msg = msgs ? s.touched + ((Qw + 3u) & ~3u) : nullptr;
     s.wsum = wsum;
     s.sc = sc;
     s.st = st;
@@ -968,14 +1037,20 @@ __global__ void k_unpack(const unsigned long long* __restrict__ packed, size_t n
 // K4: persistent, static ownership: block b owns units b, b+grid, b+2*grid, ...
 // Four 512-thread blocks per SM: occupancy (2048 threads per SM) hides the
 // memory latency of the relaxation better than more edges in flight per thread.
-template <class W>
+// PRUNE (sssp_solve_prune): a block that finds no dirty unit runs chunks of the Trishla job
+// (each warp one chunk, claimed from the header's cursor) instead of sleeping -- the paper's
+// use of the time processes spend waiting for messages (Sec. III.B) -- and goes back to its
+// doorbells after each; the chunks left when the solve ends are run by a launch after it.
+// HELD: message buffering (msg_buffer > 0), a separate instantiation so that the direct path
+// keeps its registers.
+template <class W, bool PRUNE, bool HELD>
 __global__ void __launch_bounds__(SOLVE_MAX_THREADS, 4) k_solve(SolveLaunch L) {
     extern __shared__ uint32_t dsm[];
     __shared__ uint32_t wsum[32];
     __shared__ Scalars sc;
     __shared__ unsigned long long st[ST_N];
     const uint32_t Qw = (L.Q + 31u) / 32u;
-    const Smem sm = carve(dsm, L.tile, Qw, wsum, &sc, st);
+    const Smem sm = carve(dsm, L.tile, Qw, wsum, &sc, st, HELD);
     for (uint32_t i = threadIdx.x; i < Qw; i += blockDim.x) sm.touched[i] = 0u;
     __syncthreads();
 
@@ -983,6 +1058,8 @@ __global__ void __launch_bounds__(SOLVE_MAX_THREADS, 4) k_solve(SolveLaunch L) {
         sc.backoff = 32;
         sc.idle_start = 0;
         sc.t_begin = globaltimer_ns();
+        sc.prune_done = PRUNE ? 0u : 1u;
+        sc.prune_go = 0u;
     }
     Ctx c;
     c.row_ptr = L.row_ptr;
@@ -994,6 +1071,8 @@ __global__ void __launch_bounds__(SOLVE_MAX_THREADS, 4) k_solve(SolveLaunch L) {
     c.delta = L.delta_bits;
     c.tile = L.tile;
     c.gcap = gather_cap(L.tile);
+    c.policy = L.policy;
+    c.msg_buffer = L.msg_buffer;
     c.B = L.B;
     c.Bq = L.Bq;
     c.split = L.split;
@@ -1056,7 +1135,10 @@ __global__ void __launch_bounds__(SOLVE_MAX_THREADS, 4) k_solve(SolveLaunch L) {
                         atomicExch(&L.hdr->abort_flag, 1u);
                         pick = -2;
                     }
-                    if (pick == -1) {
+                    // a block idle for a while runs a Trishla chunk instead of sleeping
+                    sc.prune_go = pick == -1 && !sc.prune_done && sc.idle_start &&
+                                  now - sc.idle_start >= PRUNE_IDLE_NS;
+                    if (pick == -1 && !sc.prune_go) {
                         __nanosleep(sc.backoff);
                         if (sc.backoff < IDLE_BACKOFF_MAX_NS) sc.backoff *= 2u;
                     }
@@ -1068,7 +1150,26 @@ __global__ void __launch_bounds__(SOLVE_MAX_THREADS, 4) k_solve(SolveLaunch L) {
         const int pick = sc.pick;
         __syncthreads();
         if (pick == -2) break;
-        if (pick < 0) continue;
+        if (pick < 0) {
+            if constexpr (PRUNE) {
+                if (sc.prune_go) {  // (written by the pick before the barrier above: the same in every thread)
+                    // each warp one chunk, its light pairs only (the heavy ones wait for the launch after
+                    // the solve), then back to the doorbells
+                    const uint32_t lane = threadIdx.x & 31u;
+                    unsigned long long ch = 0;
+                    if (lane == 0) ch = atomicAdd(&L.hdr->work_next, 1ull);
+                    ch = __shfl_sync(0xFFFFFFFFu, ch, 0);
+                    if (ch < L.prune.nchunks) {
+                        trishla_chunk<W>(L.prune, (uint32_t)ch, TRI_LIGHT);
+                        if (lane == 0) atomicAdd(&sm.st[ST_PRUNE], 1ull);
+                    } else if (lane == 0) {
+                        sc.prune_done = 1u;
+                    }
+                    __syncthreads();  // (prune_done and prune_go are next touched by the pick)
+                }
+            }
+            continue;
+        }
         const uint32_t s = (uint32_t)pick / L.Q, q = (uint32_t)pick % L.Q;
         const uint32_t p = q / L.split, k = q % L.split;
         const uint32_t plo = p * L.B;
@@ -1082,7 +1183,8 @@ __global__ void __launch_bounds__(SOLVE_MAX_THREADS, 4) k_solve(SolveLaunch L) {
         c.packed = L.packed + (size_t)s * L.V;
         c.bitmap = L.bitmap + (size_t)s * L.words;
         c.dirty = L.dirty + (size_t)s * L.Q;
-        relax_round<W, true, false>(c, lo, hi, q, sm);
+        c.nf = L.nfsplit + (size_t)s * L.Q;
+        relax_round<W, true, false, HELD>(c, lo, hi, q, sm);
     }
     __syncthreads();
     flush_stats(L.hdr, sm.st);
@@ -1103,6 +1205,9 @@ __global__ void __launch_bounds__(SOLVE_MAX_THREADS, 4) k_batched(BatchLaunch L)
     c.tile = L.tile;
     c.gcap = gather_cap(L.tile);
     c.dirty = nullptr;
+    c.nf = nullptr;
+    c.policy = SSSP_POLICY_RELATIVE;
+    c.msg_buffer = 0;
     c.ids = nullptr;
     c.B = c.Bq = c.split = 1u;
     c.Qw = 0;
@@ -1179,19 +1284,25 @@ cudaError_t set_smem(K kernel, size_t smem) {
 
 }  // namespace
 
-size_t relax_smem_bytes(uint32_t tile, uint32_t Q) {
-    return (size_t)(2u * gather_cap(tile) + 3u * tile + 1u) * 4u + (size_t)((Q + 31u) / 32u) * 4u;
+template <class W>
+const void* solve_kernel(bool prune, bool held) {
+    if (held) return prune ? (const void*)k_solve<W, true, true> : (const void*)k_solve<W, false, true>;
+    return prune ? (const void*)k_solve<W, true, false> : (const void*)k_solve<W, false, false>;
 }
 
-cudaError_t relax_max_blocks_per_sm(int wtype, uint32_t threads, uint32_t tile, uint32_t Q, int* out) {
-    const size_t smem = relax_smem_bytes(tile, Q);
+size_t relax_smem_bytes(uint32_t tile, uint32_t Q, bool msgs) {
+    size_t b = (size_t)(2u * gather_cap(tile) + 3u * tile + 1u) * 4u;
+    if (!msgs) return b + (size_t)((Q + 31u) / 32u) * 4u;
+    return b + (size_t)((((Q + 31u) / 32u) + 3u) & ~3u) * 4u + (size_t)(SOLVE_MAX_THREADS / 32u) * MSG_CAP * 4u;
+}
+
+cudaError_t relax_max_blocks_per_sm(int wtype, uint32_t threads, uint32_t tile, uint32_t Q, int* out, bool prune,
+                                    bool msgs) {
+    const size_t smem = relax_smem_bytes(tile, Q, msgs);
+    const void* k = wtype == SSSP_W_F32 ? solve_kernel<WF32>(prune, msgs) : solve_kernel<WU32>(prune, msgs);
     cudaError_t e;
-    if (wtype == SSSP_W_F32) {
-        if ((e = set_smem(k_solve<WF32>, smem)) != cudaSuccess) return e;
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_solve<WF32>, (int)threads, smem);
-    }
-    if ((e = set_smem(k_solve<WU32>, smem)) != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_solve<WU32>, (int)threads, smem);
+    if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k, (int)threads, smem);
 }
 
 cudaError_t launch_solve(const SolveLaunch& L, cudaStream_t st) {
@@ -1199,7 +1310,9 @@ cudaError_t launch_solve(const SolveLaunch& L, cudaStream_t st) {
     const size_t n_packed = (size_t)L.S * L.V;
     const size_t n_words = (size_t)L.S * L.words;
     const size_t n_dirty = (size_t)L.S * L.Q;
-    if ((e = cudaMemsetAsync(L.hdr, 0, WS_HEADER_BYTES, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(L.hdr, 0, WS_HEADER_BYTES, st)) != cudaSuccess) return e;  // (also the prune cursor)
+    if ((e = cudaMemsetAsync(L.nfsplit, 0, 4 * n_dirty, st)) != cudaSuccess) return e;
+    if (L.prune_on && (e = trishla_init(L.prune, st)) != cudaSuccess) return e;
     {
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
@@ -1224,17 +1337,16 @@ cudaError_t launch_solve(const SolveLaunch& L, cudaStream_t st) {
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    const size_t smem = relax_smem_bytes(L.tile, L.Q);
+    const size_t smem = relax_smem_bytes(L.tile, L.Q, L.msg_buffer != 0u);
     void* args[] = {const_cast<SolveLaunch*>(&L)};
     if (L.ev_begin && (e = cudaEventRecord(L.ev_begin, st)) != cudaSuccess) return e;
-    if (L.wtype == SSSP_W_F32) {
-        if ((e = set_smem(k_solve<WF32>, smem)) != cudaSuccess) return e;
-        e = cudaLaunchCooperativeKernel((const void*)k_solve<WF32>, dim3(L.grid), dim3(L.threads), args, smem, st);
-    } else {
-        if ((e = set_smem(k_solve<WU32>, smem)) != cudaSuccess) return e;
-        e = cudaLaunchCooperativeKernel((const void*)k_solve<WU32>, dim3(L.grid), dim3(L.threads), args, smem, st);
+    {
+        const bool pr = L.prune_on != 0u, held = L.msg_buffer != 0u;
+        const void* k = L.wtype == SSSP_W_F32 ? solve_kernel<WF32>(pr, held) : solve_kernel<WU32>(pr, held);
+        if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+            return e;
+        if ((e = cudaLaunchCooperativeKernel(k, dim3(L.grid), dim3(L.threads), args, smem, st)) != cudaSuccess) return e;
     }
-    if (e != cudaSuccess) return e;
     if (L.ev_end && (e = cudaEventRecord(L.ev_end, st)) != cudaSuccess) return e;
     {
         int dev = 0, sms = 0;
@@ -1246,13 +1358,16 @@ cudaError_t launch_solve(const SolveLaunch& L, cudaStream_t st) {
         else
             k_unpack<WU32><<<blocks, 256, 0, st>>>(L.packed, n_packed, L.V, L.slots, L.dist, L.pred);
     }
-    return cudaGetLastError();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // the Trishla chunks the idle blocks did not reach
+    if (L.prune_on) return trishla_launch(L.prune, L.wtype, &L.hdr->work_next, st);
+    return cudaSuccess;
 }
 
 uint32_t batched_bitmaps() { return BK_SLOTS; }
 
 cudaError_t batched_max_blocks_per_sm(int wtype, uint32_t threads, uint32_t tile, int* out) {
-    const size_t smem = relax_smem_bytes(tile, 0);
+    const size_t smem = relax_smem_bytes(tile, 0, false);
     cudaError_t e;
     if (wtype == SSSP_W_F32) {
         if ((e = set_smem(k_batched<WF32>, smem)) != cudaSuccess) return e;
@@ -1267,7 +1382,7 @@ cudaError_t launch_batched(const BatchLaunch& L, cudaStream_t st) {
     if ((e = cudaMemsetAsync(L.hdr, 0, WS_HEADER_BYTES, st)) != cudaSuccess) return e;
     // the dynamic shared-memory limit was raised by batched_max_blocks_per_sm (not a stream
     // operation, so it stays outside any graph capture)
-    const size_t smem = relax_smem_bytes(L.tile, 0);
+    const size_t smem = relax_smem_bytes(L.tile, 0, false);
     if (L.ev_begin && (e = cudaEventRecord(L.ev_begin, st)) != cudaSuccess) return e;
     if (L.wtype == SSSP_W_F32)
         k_batched<WF32><<<L.grid, L.threads, smem, st>>>(L);

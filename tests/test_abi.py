@@ -57,7 +57,8 @@ def test_host_argument_checks_without_gpu(L):
         assert L.sssp_solve(ctypes.byref(bad), 16, 1, 16, None, None, 16, 1 << 20, None) == sssp.SSSP_EINVAL
         assert L.sssp_solve_workspace_size(ctypes.byref(bad), 1, None) == 0
     # bad options
-    for o in (sssp.options(threads=100), sssp.options(threads=2048), sssp.options(tile=8), sssp.options(delta=-1)):
+    for o in (sssp.options(threads=100), sssp.options(threads=2048), sssp.options(tile=8), sssp.options(delta=-1),
+              sssp.options(policy=4), sssp.options(msg_buffer=33)):
         assert L.sssp_solve_workspace_size(ctypes.byref(g), 1, ctypes.byref(o)) == 0
     # the solve kernel runs at most 512 threads per block
     o = sssp.options(threads=1024)
@@ -149,3 +150,15 @@ def test_no_gpu_means_no_solve():
         sssp.build_csr(3, src, dst, w)
     with pytest.raises(RuntimeError, match="CUDA GPU"):
         sssp.Batch([], [])
+
+
+def test_options_layout_matches_the_header():
+    """sssp_options as the header declares it: 4 uint32, a double, a uint64, flags, policy, msg_buffer,
+    a reserved word, two pointers."""
+    O = sssp.SsspOptions
+    assert [f[0] for f in O._fields_] == ["threads", "blocks_per_sm", "tile", "split", "delta", "timeout_ns",
+                                          "flags", "policy", "msg_buffer", "reserved", "ev_relax_begin",
+                                          "ev_relax_end"]
+    assert O.delta.offset == 16 and O.timeout_ns.offset == 24 and O.policy.offset == 36
+    assert O.msg_buffer.offset == 40 and O.ev_relax_begin.offset == 48 and ctypes.sizeof(O) == 64
+    assert sssp.POLICY_NAMES == ("relative", "fixed", "near_far", "all")

@@ -1,8 +1,10 @@
 """Full-size workloads on the CUDA path, in the launch configuration the benchmark uses.
 
-For every workload the GPU CSR equals the oracle's, a sample of sources (or
-batch problems) is compared with the oracle's Dijkstra element by element,
-and every source is checked against properties that hold at any size: d(s)=0,
+For every workload the GPU CSR equals the oracle's, every source of the R-MAT,
+grid and differentiable workloads (and a sample of the 8,192 batch problems)
+is compared with the oracle's Dijkstra element by element, in the schedule
+the benchmark's autotuner picks, and every source and every batch problem is
+checked against properties that hold at any size: d(s)=0,
 d[v] <= d[u] + w(u,v) on every edge, every predecessor edge is tight, and the
 predecessor is the smallest-id tight in-neighbour.  Float32 distances must be
 bit-exact as well (both sides round each d(u)+w once).
@@ -66,14 +68,34 @@ def check_invariants(g, dist, pred, sources):
         assert bool((p[~reached & (torch.arange(V, device="cuda") != s)] == 0xFFFFFFFF).all())
 
 
-def check_oracle_sources(ref, dist, pred, sources, which):
-    for i in which:
-        d, p, _ = oracle.dijkstra(ref, int(sources[i]))
+def oracle_runs(ref, sources):
+    """The oracle's Dijkstra for every source, in threads (the C oracle runs without the GIL)."""
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(min(len(sources), 8)) as ex:
+        return list(ex.map(lambda s: oracle.dijkstra(ref, int(s))[:2], list(sources)))
+
+
+def check_oracle_sources(ref, dist, pred, sources, which=None, runs=None):
+    which = range(len(sources)) if which is None else which
+    runs = runs or oracle_runs(ref, [sources[i] for i in which])
+    for (d, p), i in zip(runs, which):
         assert np.array_equal(u32(dist[i]), d.view(np.uint32)), f"source #{i}"
         assert np.array_equal(u32(pred[i]), p), f"source #{i}"
+    return runs
 
 
-def test_rmat22_eight_sources(sssp):
+def bench_options(sssp, g, srcs, monkeypatch, tmp_path):
+    """The schedule the benchmark times: the autotuner's choice for this graph and these sources
+    (a fresh cache, as on a fresh machine)."""
+    monkeypatch.setenv("SSSP_TUNE_CACHE", str(tmp_path / "tune.json"))
+    opts, ms = sssp.autotune(g, srcs)
+    assert ms is not None
+    return opts
+
+
+def test_rmat22_eight_sources(sssp, monkeypatch, tmp_path):
+    """All 8 sources element by element against the oracle, on the graph as built and on the
+    locality layout the benchmark solves on, in the benchmark's autotuned schedule."""
     g0, srcs, P = gg.workload_rmat22()
     ref = oracle.csr_of(g0)
     g = sssp.build_csr(g0.V, g0.src, g0.dst, g0.w, partitions=P)
@@ -81,7 +103,7 @@ def test_rmat22_eight_sources(sssp):
     del g0
     dist, pred, st, stats = sssp.solve(g, srcs)
     assert st == sssp.SSSP_OK
-    check_oracle_sources(ref, dist, pred, srcs, [0, len(srcs) - 1])
+    runs = check_oracle_sources(ref, dist, pred, srcs)
     check_invariants(g, dist, pred, srcs.tolist())
     # the benchmark solves on the locality layout: the renaming equals the oracle's, and the
     # solve on it returns the same distances and canonical predecessors, in the caller's ids
@@ -91,21 +113,25 @@ def test_rmat22_eight_sources(sssp):
     check_csr_equal(h, rh)
     assert np.array_equal(u32(h.eid), rh.eid)
     del rh
-    dist2, pred2, st, _ = sssp.solve(h, srcs)
+    opts = bench_options(sssp, h, srcs, monkeypatch, tmp_path)
+    dist2, pred2, st, _ = sssp.solve(h, srcs, opts)
     assert st == sssp.SSSP_OK
-    assert torch.equal(dist2, dist) and torch.equal(pred2, pred)
-    check_oracle_sources(ref, dist2, pred2, srcs, [1])
+    check_oracle_sources(ref, dist2, pred2, srcs, runs=runs)
 
 
-def test_grid4096_corner(sssp):
+def test_grid4096_corner(sssp, monkeypatch, tmp_path):
+    """The grid in the benchmark's autotuned schedule (and in a fixed wide-bucket one)."""
     g0, srcs, P = gg.workload_grid4096()
     ref = oracle.csr_of(g0)
     g = sssp.build_csr(g0.V, g0.src, g0.dst, g0.w, partitions=P)
     check_csr_equal(g, ref)
     del g0
-    dist, pred, st, stats = sssp.solve(g, srcs, sssp.options(delta=2048, tile=4096))
-    assert st == sssp.SSSP_OK
-    check_oracle_sources(ref, dist, pred, srcs, [0])
+    opts = bench_options(sssp, g, srcs, monkeypatch, tmp_path)
+    runs = None
+    for o in (opts, sssp.options(delta=2048, tile=4096)):
+        dist, pred, st, stats = sssp.solve(g, srcs, o)
+        assert st == sssp.SSSP_OK
+        runs = check_oracle_sources(ref, dist, pred, srcs, runs=runs)
     check_invariants(g, dist, pred, srcs.tolist())
 
 
@@ -181,17 +207,19 @@ def test_rmat22_trishla_witnesses_and_sampled_completeness(sssp):
     assert int(pruned[se].sum()) > 0
 
 
-def test_rmat18_f32_forward_backward(sssp):
+def test_rmat18_f32_forward_backward(sssp, monkeypatch, tmp_path):
+    """The differentiable workload as the benchmark runs it: 16 partitions, autotuned schedule."""
     g0, srcs, gup = gg.workload_rmat18_f32()
     ref = oracle.csr_of(g0)
-    g = sssp.build_csr(g0.V, g0.src, g0.dst, g0.w, partitions=8)
+    g = sssp.build_csr(g0.V, g0.src, g0.dst, g0.w, partitions=16)
     check_csr_equal(g, ref)
-    dist, pred, st, _ = sssp.solve(g, srcs)
+    opts = bench_options(sssp, g, srcs, monkeypatch, tmp_path)
+    dist, pred, st, _ = sssp.solve(g, srcs, opts)
     assert st == sssp.SSSP_OK
     rd = np.empty((len(srcs), g.V), np.float32)
     rp = np.empty((len(srcs), g.V), np.uint32)
-    for i, s in enumerate(srcs):
-        rd[i], rp[i], _ = oracle.dijkstra(ref, int(s))
+    for i, (d, p) in enumerate(oracle_runs(ref, srcs)):
+        rd[i], rp[i] = d, p
     assert np.array_equal(u32(dist), rd.view(np.uint32))
     assert np.array_equal(u32(pred), rp)
     check_invariants(g, dist, pred, srcs.tolist())
@@ -202,7 +230,7 @@ def test_rmat18_f32_forward_backward(sssp):
     assert (grad[rg == 0] == 0).all()
 
 
-def test_batch512_sampled(sssp):
+def test_batch512_sampled_and_certified(sssp):
     graphs0, sources = gg.workload_batch512()
     graphs = [oracle.csr_of(g) for g in graphs0]
     del graphs0
@@ -218,19 +246,15 @@ def test_batch512_sampled(sssp):
         d, p, _ = oracle.dijkstra(graphs[gi], s)
         bd, bp = b.result(i)
         assert np.array_equal(u32(bd), d) and np.array_equal(u32(bp), p), (i, gi, s)
-    # every problem: d(s) = 0 and the predecessor of each reached vertex is tight (vectorised per graph)
-    for i in range(0, b.n_problems, 97):
-        gi, s = int(b.prob_graph[i]), int(b.prob_source[i])
-        bd, bp = b.result(i)
-        d = u32(bd).astype(np.int64)
-        p = u32(bp).astype(np.int64)
-        assert d[s] == 0
+    # every one of the 8,192 problems: the full certificate (d(s) = 0, every edge relaxed, the
+    # predecessor the smallest tight in-neighbour, unreached vertices unlabelled), per graph on
+    # the device over its 16 problems at once
+    first = {}
+    for i in range(b.n_problems):
+        first.setdefault(int(b.prob_graph[i]), []).append(i)
+    for gi, probs in first.items():
         G = graphs[gi]
-        reached = (d != 0xFFFFFFFF)
-        reached[s] = False
-        vs = np.nonzero(reached)[0]
-        for v in vs[:200]:
-            u = p[v]
-            lo, hi = G.row_ptr[u], G.row_ptr[u + 1]
-            k = lo + np.searchsorted(G.col[lo:hi], v)
-            assert G.col[k] == v and d[u] + int(G.w[k]) == d[v]
+        gd = sssp.upload_csr(G.V, G.row_ptr, G.col, G.w)
+        dist = torch.stack([b.result(i)[0] for i in probs])
+        pred = torch.stack([b.result(i)[1] for i in probs])
+        check_invariants(gd, dist, pred, [int(b.prob_source[i]) for i in probs])

@@ -163,6 +163,53 @@ def test_prune_parity_dense_and_f32(sssp, seed, V, E, P, mode, f32):
     assert np.array_equal(u32(wit), rw)
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("f32", [False, True])
+def test_solve_prune_equals_solve_and_prune(sssp, mode, f32):
+    """sssp_solve_prune: idle blocks of the solve run Trishla chunks (the rest right after the
+    solve); the keep mask and least witnesses equal the oracle's Algorithm 1 and the distances
+    and predecessors equal its Dijkstra.  Many partitions and few sources leave blocks idle."""
+    V = 6000
+    src, dst, w = raw_graph(90 + mode, V, 90000, f32=f32)
+    ref = oracle.csr(V, src, dst, w)
+    P = 40
+    g = sssp.build_csr(V, src, dst, w, partitions=P)
+    srcs = [0, 5999]
+    dist, pred, keep, wit, st, _ = sssp.solve_prune(g, np.array(srcs, np.uint32), mode, sssp.options(split=2))
+    assert st == sssp.SSSP_OK
+    rk, rw = oracle.trishla(ref, P, mode)
+    assert np.array_equal(keep.cpu().numpy(), rk) and np.array_equal(u32(wit), rw)
+    assert (rk == 0).sum() > 0
+    for i, s_ in enumerate(srcs):
+        d, p, _ = oracle.dijkstra(ref, s_)
+        assert np.array_equal(u32(dist[i]), d.view(np.uint32)) and np.array_equal(u32(pred[i]), p)
+    # without a witness array: the same keep mask and result
+    d2, p2, k2, w2, st, _ = sssp.solve_prune(g, np.array(srcs, np.uint32), mode, witness=False)
+    assert st == sssp.SSSP_OK and w2 is None
+    assert np.array_equal(k2.cpu().numpy(), rk) and torch.equal(d2, dist) and torch.equal(p2, pred)
+
+
+def test_solve_prune_er16k_and_grid(sssp):
+    """The paper's configuration (ER 16K, 4 partitions, local Trishla) and a grid, where
+    Trishla finds nothing to prune (no triangles) but most blocks are idle."""
+    g0, srcs, P = gg.workload_er16k()
+    ref = oracle.csr_of(g0)
+    g = sssp.build_csr(g0.V, g0.src, g0.dst, g0.w, partitions=P)
+    dist, pred, keep, wit, st, _ = sssp.solve_prune(g, srcs, 0)
+    assert st == sssp.SSSP_OK
+    rk, rw = oracle.trishla(ref, P, 0)
+    assert np.array_equal(keep.cpu().numpy(), rk) and np.array_equal(u32(wit), rw)
+    d, p, _ = oracle.dijkstra(ref, int(srcs[0]))
+    assert np.array_equal(u32(dist[0]), d) and np.array_equal(u32(pred[0]), p)
+    gr = gg.grid(gg.BASE_SEED + 95, 256, 256, 1, 1000)
+    rg = oracle.csr_of(gr)
+    G = sssp.build_csr(gr.V, gr.src, gr.dst, gr.w, partitions=64)
+    dist, pred, keep, wit, st, _ = sssp.solve_prune(G, np.array([0], np.uint32), 1)
+    assert st == sssp.SSSP_OK and bool((keep == 1).all()) and bool((wit == -1).all())
+    d, p, _ = oracle.dijkstra(rg, 0)
+    assert np.array_equal(u32(dist[0]), d) and np.array_equal(u32(pred[0]), p)
+
+
 def test_compact_and_solve_on_pruned_graph(sssp):
     g0, srcs, P = gg.workload_er16k()
     ref = oracle.csr_of(g0)
@@ -191,12 +238,83 @@ def test_solve_er16k_p4(sssp):
 
 @pytest.mark.parametrize("P", [1, 2, 4, 7, 148])
 @pytest.mark.parametrize("split", [1, 3])
-def test_solve_partition_counts(sssp, P, split):
+@pytest.mark.parametrize("f32", [False, True])
+@pytest.mark.parametrize("policy", [0, 1, 2, 3])
+def test_solve_partition_counts(sssp, P, split, f32, policy):
+    """Every frontier policy (relative, fixed, near-far, all) on every partition count and split,
+    uint32 and float32 weights: the same distances and predecessors as the oracle."""
     V = 5000
-    src, dst, w = raw_graph(30 + P, V, 40000)
+    src, dst, w = raw_graph(30 + P, V, 40000, f32=f32)
     ref = oracle.csr(V, src, dst, w)
     g = sssp.build_csr(V, src, dst, w, partitions=P)
-    check_solve(sssp, g, ref, [0, 4999, 2500, 0], sssp.options(split=split))
+    delta = 0.1 if f32 else 16
+    check_solve(sssp, g, ref, [0, 4999, 2500, 0], sssp.options(split=split, policy=policy, delta=delta))
+
+
+@pytest.mark.parametrize("msg", [1, 8, 32])
+@pytest.mark.parametrize("P,split", [(7, 1), (148, 1), (37, 3)])
+@pytest.mark.parametrize("f32", [False, True])
+def test_message_buffering_gives_the_same_result(sssp, msg, P, split, f32):
+    """Messages held per warp and pushed out at msg of them and at the end of each sub-round:
+    the oracle's distances and predecessors for every buffer size, partitioning and weight type."""
+    V = 20000
+    src, dst, w = raw_graph(50 + P, V, 200000, f32=f32)
+    ref = oracle.csr(V, src, dst, w)
+    g = sssp.build_csr(V, src, dst, w, partitions=P)
+    stats = check_solve(sssp, g, ref, [0, 19999, 777], sssp.options(split=split, msg_buffer=msg,
+                                                                     delta=0.25 if f32 else 16))
+    assert stats["remote_activations"] > 0
+
+
+def test_message_buffering_with_layout_policies_and_warm_start(sssp):
+    g0 = gg.rmat(gg.BASE_SEED + 620, 14, 16 << 14)
+    ref = oracle.csr_of(g0)
+    g = sssp.build_csr(g0.V, g0.src, g0.dst, g0.w, partitions=64)
+    srcs = gg.pick_sources(gg.BASE_SEED + 620, g0, 4)
+    for pol in range(4):
+        check_solve(sssp, sssp.layout(g), ref, srcs.tolist(), sssp.options(policy=pol, msg_buffer=16, delta=6))
+    src, dst, w = raw_graph(621, 8000, 64000, loops=False)
+    s2, d2, w2, tails = _lowered(622, src, dst, w, 8000)
+    g1 = sssp.build_csr(8000, src, dst, w, partitions=16)
+    g2 = sssp.build_csr(8000, s2, d2, w2, partitions=16)
+    o = sssp.options(msg_buffer=4)
+    d, p, st, _ = sssp.solve(g1, np.array([5, 77], np.uint32), o)
+    d, p, st, _ = sssp.update(g2, d, p, tails, o)
+    assert st == sssp.SSSP_OK
+    ref2 = oracle.csr(8000, s2, d2, w2)
+    for i, s_ in enumerate((5, 77)):
+        rd, rp, _ = oracle.dijkstra(ref2, s_)
+        assert np.array_equal(u32(d[i]), rd) and np.array_equal(u32(p[i]), rp)
+
+
+@pytest.mark.parametrize("policy", [0, 1, 2, 3])
+def test_policies_on_layout_grid_and_warm_start(sssp, policy):
+    """The policies on a layout graph (skewed R-MAT), on a grid whose distances have a closed form
+    (constant weights: c * (r + col) from the corner), and in a warm start."""
+    g0 = gg.rmat(gg.BASE_SEED + 610, 13, 16 << 13)
+    ref = oracle.csr_of(g0)
+    g = sssp.build_csr(g0.V, g0.src, g0.dst, g0.w, partitions=37)
+    srcs = gg.pick_sources(gg.BASE_SEED + 610, g0, 4)
+    check_solve(sssp, sssp.layout(g), ref, srcs.tolist(), sssp.options(policy=policy, delta=8, split=2))
+    side, c = 300, 7
+    gr = gg.grid(gg.BASE_SEED + 611, side, side, c, c)
+    G = sssp.build_csr(gr.V, gr.src, gr.dst, gr.w, partitions=12)
+    dist, pred, st, _ = sssp.solve(G, np.array([0], np.uint32), sssp.options(policy=policy, delta=3 * c))
+    assert st == sssp.SSSP_OK
+    r, q = np.divmod(np.arange(side * side), side)
+    assert np.array_equal(u32(dist[0]), (c * (r + q)).astype(np.uint32))
+    src, dst, w = raw_graph(612, 8000, 64000, loops=False)
+    s2, d2, w2, tails = _lowered(613, src, dst, w, 8000)
+    g1 = sssp.build_csr(8000, src, dst, w, partitions=16)
+    g2 = sssp.build_csr(8000, s2, d2, w2, partitions=16)
+    o = sssp.options(policy=policy, delta=12)
+    d, p, st, _ = sssp.solve(g1, np.array([5, 77], np.uint32), o)
+    d, p, st, _ = sssp.update(g2, d, p, tails, o)
+    assert st == sssp.SSSP_OK
+    ref2 = oracle.csr(8000, s2, d2, w2)
+    for i, s_ in enumerate((5, 77)):
+        rd, rp, _ = oracle.dijkstra(ref2, s_)
+        assert np.array_equal(u32(d[i]), rd) and np.array_equal(u32(p[i]), rp)
 
 
 @pytest.mark.parametrize("opts", [dict(threads=128, tile=32, delta=1), dict(threads=256, tile=64, delta=10),
@@ -389,10 +507,11 @@ def test_autotune_picks_a_valid_schedule_and_caches_it(sssp, tmp_path, monkeypat
     srcs = np.array([1, 2, 29999], np.uint32)
     opts, ms = sssp.autotune(g, srcs)
     assert ms is not None and ms > 0 and opts.delta >= 1 and opts.tile in (1024, 2048, 4096)
-    assert opts.split in (1, 2, 4)
+    assert opts.split in (1, 2, 4) and opts.policy in (0, 1, 2, 3)
     check_solve(sssp, g, ref, srcs.tolist(), opts)
     again, ms2 = sssp.autotune(g, srcs)
-    assert ms2 is None and (again.delta, again.tile, again.split) == (opts.delta, opts.tile, opts.split)
+    assert ms2 is None and (again.delta, again.tile, again.split, again.policy) == (opts.delta, opts.tile, opts.split,
+                                                                                    opts.policy)
 
 
 # ------------------------------------------------------------------------ K5

@@ -1,8 +1,11 @@
-"""The multi-GPU path of bench.py on CPU: two gloo ranks (no GPU, no NCCL).
+"""The multi-GPU paths on CPU: two gloo ranks (no GPU, no NCCL).
 
 Sources shard across ranks with no exchange on the data path (each rank
 solves its own 8 sources); only the per-step time is reduced (MAX over ranks)
-and the traversed-edge counts summed, as bench.py does under torchrun.
+and the traversed-edge counts summed, as bench.py does under torchrun.  The
+batched form shards its (graph, source) problems with the library's planner
+(sssp_shard_problems, host only), and the differentiable form shards its
+sources and sums dL/dw over the ranks with one all-reduce.
 """
 import os
 import socket
@@ -61,3 +64,81 @@ def test_two_ranks_shard_sources_and_reduce_timing():
     g = gg.rmat(gg.BASE_SEED + 900, 12, 16 << 12)
     import bench
     assert bench.rank_sources(g, 0).tolist() == s0
+
+
+def _shard_worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    import torch
+
+    import oracle
+    import paper_2103_12012_gb300 as sssp
+
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    # batched form: the full 512-graph recipe, 16 sources per graph
+    graphs, sources = gg.workload_batch512()
+    keep_g, keep_s = sssp.shard_batch(graphs, sources, rank, world)
+    mine = [(g, int(s)) for g, ss in zip(keep_g, keep_s) for s in ss.tolist()]
+    load = sum(int(graphs[g].E_raw) + int(graphs[g].V) for g, _ in mine)
+    # differentiable form: float32 R-MAT, 8 sources dealt out over the ranks; each rank's
+    # dL/dw (the oracle's tree gradient over its own sources) summed by one all-reduce
+    gf = gg.rmat(gg.BASE_SEED + 901, 9, 8 << 9, wf32=(0.5, 2.0, 1e-4))
+    ref = oracle.csr_of(gf)
+    srcs = gg.pick_sources(gg.BASE_SEED + 901, gf, 8)
+    gup = gg.normal_f32(11, (len(srcs), ref.V))
+    idx = sssp.shard_sources(len(srcs), rank, world)
+    d = np.stack([oracle.dijkstra(ref, int(srcs[i]))[0] for i in idx])
+    p = np.stack([oracle.dijkstra(ref, int(srcs[i]))[1] for i in idx])
+    grad = torch.from_numpy(oracle.tree_grad(ref, d, p, gup[idx]))
+    sssp.allreduce_sum(grad)
+    out[rank] = (mine, load, idx.tolist(), grad.numpy())
+    dist.destroy_process_group()
+
+
+def test_two_ranks_shard_the_batch_and_sum_the_gradient():
+    world = 2
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    port = _free_port()
+    mp.start_processes(_shard_worker, args=(world, port, out), nprocs=world, start_method="spawn", join=True)
+    res = [out[r] for r in range(world)]
+    graphs, sources = gg.workload_batch512()
+    every = [(g, int(s)) for g, ss in enumerate(sources) for s in np.asarray(ss).tolist()]
+    got = res[0][0] + res[1][0]
+    # disjoint and complete: every (graph, source) problem solved by exactly one rank
+    assert sorted(got) == sorted(every) and len(got) == 512 * 16
+    assert not set(res[0][0]) & set(res[1][0])
+    # balanced by estimated edges: the ranks differ by at most the largest single problem
+    biggest = max(int(g.E_raw) + int(g.V) for g in graphs)
+    assert abs(res[0][1] - res[1][1]) <= biggest
+    assert abs(res[0][1] - res[1][1]) / (res[0][1] + res[1][1]) < 0.01
+    # gradient: sources split without overlap, and the all-reduced sum equals the whole
+    assert sorted(res[0][2] + res[1][2]) == list(range(8)) and not set(res[0][2]) & set(res[1][2])
+    import oracle
+    gf = gg.rmat(gg.BASE_SEED + 901, 9, 8 << 9, wf32=(0.5, 2.0, 1e-4))
+    ref = oracle.csr_of(gf)
+    srcs = gg.pick_sources(gg.BASE_SEED + 901, gf, 8)
+    gup = gg.normal_f32(11, (len(srcs), ref.V))
+    d = np.stack([oracle.dijkstra(ref, int(s))[0] for s in srcs])
+    p = np.stack([oracle.dijkstra(ref, int(s))[1] for s in srcs])
+    whole = oracle.tree_grad(ref, d, p, gup)
+    for r in range(world):
+        assert np.allclose(res[r][3], whole, rtol=1e-12, atol=1e-12)
+    assert np.abs(whole).sum() > 0
+
+
+def test_planner_assignments():
+    """sssp_shard_problems: longest first to the least loaded rank (ties: lowest index, lowest
+    rank); the largest load stays within the mean plus the largest cost; bad arguments refused."""
+    import paper_2103_12012_gb300 as sssp
+    rank_of, load = sssp.shard_problems([5, 5, 4, 3, 3, 2, 2, 2], 3)
+    assert rank_of.tolist() == [0, 1, 2, 2, 0, 1, 1, 2] and load.tolist() == [8, 9, 9]
+    rng = np.random.default_rng(3)
+    for world in (1, 2, 3, 8):
+        c = rng.integers(1, 10 ** 6, 1000)
+        r, ld = sssp.shard_problems(c, world)
+        assert r.max() < world and ld.sum() == c.sum()
+        assert np.array_equal(np.bincount(r, weights=c, minlength=world).astype(np.uint64), ld)
+        assert ld.max() <= c.sum() / world + c.max()
+    assert sssp.shard_sources(8, 1, 3).tolist() == [1, 4, 7]
+    with pytest.raises(sssp.SsspError):
+        sssp.shard_problems([1, 2], 0)
