@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--split", type=int, default=0)
     ap.add_argument("--no-tune", action="store_true", help="library defaults instead of the autotuned schedule")
-    ap.add_argument("--profile-case", choices=["batched", "backward", "prune", "grid", "all"],
+    ap.add_argument("--profile-case", choices=["batched", "batched-full", "backward", "prune", "grid", "all"],
                     help="run a small case of one kernel three times and exit (for ncu captures)")
     return ap.parse_args()
 
@@ -721,28 +721,43 @@ def extras_differentiable(sssp, dev, rank=0, world=1):
             "fwd_bwd_over_fwd": round(ms_both / ms_fwd, 3)}
 
 
-def tree_depth(pred):
-    """Edges on the longest tree path (the hops of the deepest shortest path) of each predecessor
-    row, by pointer doubling on the device."""
+def tree_path_sums(pred, weight=None):
+    """For every vertex, the sum of `weight` (default 1) over the tree edges on its path to the
+    root, one row of predecessors at a time (pointer doubling on the device); weight[v] belongs
+    to the edge (pred[v], v)."""
     import torch
     p = pred.long() & 0xFFFFFFFF
     none = p == 0xFFFFFFFF
     anc = torch.where(none, torch.arange(p.shape[-1], device=p.device).expand_as(p), p)
-    dep = (~none).long()
+    dep = (~none).long() if weight is None else weight.long() * (~none).long()
     for _ in range(int(p.shape[-1]).bit_length()):
         dep = dep + torch.gather(dep, -1, anc) * (anc != torch.gather(anc, -1, anc)).long()
         anc = torch.gather(anc, -1, anc)
-    return dep.max(dim=-1).values
+    return dep
 
 
-def chain_ms_per_hop(sssp, dev, n=1 << 16, partitions=1, reps=3):
-    """ms per hop of a pure chain 0 -> 1 -> ... -> n-1 (unit weights): every hop waits for the one
-    before it, inside one unit (partitions=1: a sub-round each) or crossing units."""
+def tree_depth(pred):
+    """Edges on the longest tree path (the hops of the deepest shortest path) of each row."""
+    return tree_path_sums(pred).max(dim=-1).values
+
+
+def chain_ms_per_hop(sssp, dev, n=1 << 16, partitions=1, cross=False, reps=3):
+    """ms per hop of a pure chain of n vertices (unit weights): every hop waits for the one before
+    it.  cross=False: the chain runs through consecutive ids (inside one unit when partitions=1,
+    a sub-round per hop); cross=True: consecutive chain vertices lie in different partitions, so
+    every hop is a message to another unit."""
     import torch
-    v = np.arange(n - 1, dtype=np.uint32)
-    g = sssp.build_csr(n, v, v + 1, np.ones(n - 1, np.uint32), partitions=partitions)
+    if cross:
+        n -= n % partitions  # whole blocks: B = n / partitions, every node id below n
+    i = np.arange(n, dtype=np.int64)
+    if cross:
+        B = n // partitions
+        node = ((i % partitions) * B + i // partitions).astype(np.uint32)
+    else:
+        node = i.astype(np.uint32)
+    g = sssp.build_csr(n, node[:-1], node[1:], np.ones(n - 1, np.uint32), partitions=partitions)
     solver = sssp.Solver(g, 1, sssp.options(delta=1e9))
-    src = torch.zeros(1, dtype=torch.int32, device=dev)
+    src = torch.full((1,), int(node[0]), dtype=torch.int32, device=dev)
     solver.launch(src)
     st, _ = solver.status()
     assert st == sssp.SSSP_OK
@@ -751,9 +766,10 @@ def chain_ms_per_hop(sssp, dev, n=1 << 16, partitions=1, reps=3):
 
 def extras_grid(sssp, dev):
     """4096 x 4096 grid, corner source: the high-diameter case (autotuned schedule).  Latency model:
-    the deepest shortest path has `depth` hops, each of which waits for the one before it; a pure
-    chain solved inside one unit gives the least time per hop this solve takes (one sub-round),
-    so depth x that time is the floor of the grid's solve in this design."""
+    the deepest shortest path has `depth` hops, each of which waits for the one before it, and
+    `crossing` of them lead into another unit; pure chains give the time of a hop inside a unit
+    (a sub-round) and across units (a message, its doorbell and the owner's round), so
+    (depth - crossing) x t_in + crossing x t_cross is the floor of the grid's solve here."""
     import torch
     g0, srcs, P = gg.workload_grid4096()
     g = sssp.build_csr(g0.V, g0.src, g0.dst, g0.w, partitions=P)
@@ -765,12 +781,25 @@ def extras_grid(sssp, dev):
     st, stats = solver.status()
     assert st == sssp.SSSP_OK
     ms = _time_ms(lambda: solver.launch(src_d), 3)
-    depth = int(tree_depth(solver.pred)[0].item())
+    # the deepest path's hops, and how many of them cross from one unit to another
+    V = g.V
+    B = -(-V // g.partitions)
+    split = opts.split or 1
+    Bq = -(-B // split)
+    v = torch.arange(V, device=dev)
+    unit = (v // B) * split + (v % B) // Bq
+    p = solver.pred[0].long() & 0xFFFFFFFF
+    crosses = (p != 0xFFFFFFFF) & (unit[p.clamp(max=V - 1)] != unit)
+    hops = tree_path_sums(solver.pred)[0]
+    deep = int(torch.argmax(hops))
+    depth = int(hops[deep])
+    n_cross = int(tree_path_sums(solver.pred, crosses[None, :])[0][deep])
     hop_in = chain_ms_per_hop(sssp, dev, partitions=1)
-    hop_cross = chain_ms_per_hop(sssp, dev, partitions=148)
-    model = {"depth_hops": depth, "ms_per_hop": round(ms / depth, 6),
-             "chain_ms_per_hop_in_unit": round(hop_in, 6), "chain_ms_per_hop_148_units": round(hop_cross, 6),
-             "floor_ms": round(depth * hop_in, 3), "measured_over_floor": round(ms / (depth * hop_in), 2)}
+    hop_cross = chain_ms_per_hop(sssp, dev, partitions=148, cross=True)
+    floor = (depth - n_cross) * hop_in + n_cross * hop_cross
+    model = {"depth_hops": depth, "crossing_hops": n_cross, "ms_per_hop": round(ms / depth, 6),
+             "chain_ms_per_hop_in_unit": round(hop_in, 6), "chain_ms_per_hop_across_units": round(hop_cross, 6),
+             "floor_ms": round(floor, 3), "measured_over_floor": round(ms / floor, 2)}
     return {"workload": "grid 4096x4096, corner source", "delta": opts.delta, "tile": opts.tile,
             "latency_model": model,
             "split": opts.split, "policy": sssp.POLICY_NAMES[opts.policy], "ms": round(ms, 3),
@@ -969,6 +998,17 @@ def profile_case(which):
         gr = sssp.backward(gf, fpred, torch.from_numpy(gup).cuda())
         torch.cuda.synchronize()
         print("all", g.E, h.E, gp.E, float(gr.abs().sum()))
+    elif which == "batched-full":
+        # the full 512-graph, 16-source batch at the schedule the bench's tuner picks (delta 8, tile 1024)
+        graphs0, sources = gg.workload_batch512()
+        graphs = [sssp.build_csr(x.V, x.src, x.dst, x.w) for x in graphs0]
+        del graphs0
+        b = sssp.Batch(graphs, sources, sssp.options(delta=8, tile=1024))
+        for _ in range(2):
+            b.solve()
+        st, stats = b.status()
+        assert st == sssp.SSSP_OK, st
+        print("batched-full", b.n_problems, stats)
     elif which == "batched":
         graphs0, sources = gg.workload_batch512(n_graphs=64)
         graphs = [sssp.build_csr(g.V, g.src, g.dst, g.w) for g in graphs0]
