@@ -593,6 +593,24 @@ def test_batched_equals_single_solves(sssp):
         assert torch.equal(bd, dist[i]) and torch.equal(bp, pred[i])
 
 
+@pytest.mark.parametrize("threads,tile", [(128, 1024), (128, 64), (256, 256), (256, 4096), (512, 512), (384, 32)])
+def test_batched_block_sizes(sssp, threads, tile):
+    """The batched kernel with every block size and tile: blocks smaller or larger than the tile
+    and than half of it (the small sub-round path keeps its entries in tile halves)."""
+    graphs = [oracle.csr_of(gg.rmat(gg.BASE_SEED + 700 + k, 11 + k % 3, 8 << (11 + k % 3))) for k in range(4)]
+    graphs.append(oracle.csr_of(gg.erdos_renyi(gg.BASE_SEED + 710, 3000, 24000, 1, 255)))
+    srcs = [np.array([0, 1, g.V - 1], np.uint32) for g in graphs]
+    b = sssp.Batch(graphs, srcs, sssp.options(threads=threads, tile=tile, delta=8))
+    b.solve()
+    st, _ = b.status()
+    assert st == sssp.SSSP_OK
+    for i in range(b.n_problems):
+        gi, s_ = int(b.prob_graph[i]), int(b.prob_source[i])
+        d, p, _ = oracle.dijkstra(graphs[gi], s_)
+        bd, bp = b.result(i)
+        assert np.array_equal(u32(bd), d) and np.array_equal(u32(bp), p), (threads, tile, i)
+
+
 @pytest.mark.parametrize("f32", [False, True])
 @pytest.mark.parametrize("opts", [dict(delta=1e6), dict(delta=1e6, tile=256), dict(delta=1)])
 def test_batched_small_and_general_subround_mix(sssp, f32, opts):
