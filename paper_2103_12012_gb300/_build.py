@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libsssp.so")
-SOURCES = ["api.cu", "relax.cu", "csr.cu", "prune.cu", "backward.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "relax.cu", "csr.cu", "prune.cu", "backward.cu", "noalloc.cu", "sort.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

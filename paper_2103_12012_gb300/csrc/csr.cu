@@ -6,11 +6,9 @@
 // keys become one edge whose weight is the run's minimum (lowest input index
 // on ties, via a 64-bit atomicMin on (weight bits << 32 | index)), and
 // row_ptr is filled from the run boundaries.  Self-loops and bad ids sort to
-// the end behind a sentinel key and are dropped.  The radix sort and prefix
-// sums are CUB library primitives; the rest is hand-written here.
+// the end behind a sentinel key and are dropped.  The radix sort and the
+// prefix sums are this library's own (sort.cu).
 #include <algorithm>
-#include <cub/device/device_radix_sort.cuh>
-#include <cub/device/device_scan.cuh>
 
 #include "common.cuh"
 #include "internal.h"
@@ -30,18 +28,9 @@ struct CsrWs {
     uint32_t *vals_in, *vals_out;
     uint32_t* runinc;             // [E_raw] inclusive run index
     unsigned long long* runbest;  // [E_raw] (weight bits << 32 | input index)
-    void* cub_tmp;
-    size_t cub_bytes;
+    void* tmp;                    // sort and scan temporaries
     size_t total;
 };
-
-size_t cub_bytes_for(uint64_t n) {
-    size_t a = 0, b = 0;
-    cub::DeviceRadixSort::SortPairs(nullptr, a, (unsigned long long*)nullptr, (unsigned long long*)nullptr,
-                                    (uint32_t*)nullptr, (uint32_t*)nullptr, (int64_t)n, 0, 64);
-    cub::DeviceScan::InclusiveSum(nullptr, b, (uint32_t*)nullptr, (uint32_t*)nullptr, (int64_t)n);
-    return std::max(a, b);
-}
 
 CsrWs carve_csr(void* ws, uint32_t V, uint64_t n) {
     (void)V;
@@ -60,8 +49,7 @@ CsrWs carve_csr(void* ws, uint32_t V, uint64_t n) {
     c.vals_out = reinterpret_cast<uint32_t*>(take(4 * n));
     c.runinc = reinterpret_cast<uint32_t*>(take(4 * n));
     c.runbest = reinterpret_cast<unsigned long long*>(take(8 * n));
-    c.cub_bytes = cub_bytes_for(n);
-    c.cub_tmp = take(c.cub_bytes);
+    c.tmp = take(std::max(sort_temp_bytes(n), scan_temp_bytes(n)));
     c.total = off;
     return c;
 }
@@ -297,17 +285,18 @@ sssp_status csr_build(uint32_t V, uint64_t n, const uint32_t* src, const uint32_
     else
         k_make_keys<WU32><<<g, 256, 0, st>>>(V, n, src, dst, w, c.keys_in, c.vals_in, c.hdr);
     CK(cudaGetLastError());
-    size_t tb = c.cub_bytes;
-    CK(cub::DeviceRadixSort::SortPairs(c.cub_tmp, tb, c.keys_in, c.keys_out, c.vals_in, c.vals_out, (int64_t)n, 0,
-                                       end_bit, st));
-    k_heads<<<g, 256, 0, st>>>(n, sentinel, c.keys_out, c.vals_in);  // vals_in reused as head flags
+    bool second = false;
+    CK(sort_pairs_u64(c.tmp, c.keys_in, c.keys_out, c.vals_in, c.vals_out, n, end_bit, st, &second));
+    const unsigned long long* sk = second ? c.keys_out : c.keys_in;  // sorted pairs
+    const uint32_t* sv = second ? c.vals_out : c.vals_in;
+    uint32_t* heads = second ? c.vals_in : c.vals_out;  // the other value buffer: head flags
+    k_heads<<<g, 256, 0, st>>>(n, sentinel, sk, heads);
     CK(cudaGetLastError());
-    tb = c.cub_bytes;
-    CK(cub::DeviceScan::InclusiveSum(c.cub_tmp, tb, c.vals_in, c.runinc, (int64_t)n, st));
+    CK(inclusive_scan_u32(c.tmp, heads, c.runinc, n, st));
     CK(cudaMemsetAsync(c.runbest, 0xFF, 8 * n, st));
-    k_run_min<<<g, 256, 0, st>>>(n, sentinel, c.keys_out, c.vals_out, w, c.runinc, c.runbest);
+    k_run_min<<<g, 256, 0, st>>>(n, sentinel, sk, sv, w, c.runinc, c.runbest);
     CK(cudaGetLastError());
-    k_emit<<<g, 256, 0, st>>>(V, n, sentinel, c.keys_out, c.runinc, c.runbest, row_ptr, col, w_out, eid, E_out);
+    k_emit<<<g, 256, 0, st>>>(V, n, sentinel, sk, c.runinc, c.runbest, row_ptr, col, w_out, eid, E_out);
     CK(cudaGetLastError());
     return SSSP_OK;
 }
@@ -328,17 +317,14 @@ cudaError_t partition_launch(const sssp_graph* g, uint32_t* bounds, uint64_t* in
 
 namespace {
 struct LayoutWs {
-    size_t off_deg, off_kin, off_kout, off_vin, off_vout, off_cub, off_src, off_dst, off_eout, total;
-    size_t csr_bytes, cub_bytes;
+    size_t off_deg, off_kin, off_kout, off_vin, off_vout, off_tmp, off_src, off_dst, off_eout, total;
+    size_t csr_bytes, tmp_bytes;
 };
 
 LayoutWs layout_ws(uint32_t V, uint32_t E) {
     LayoutWs w{};
     w.csr_bytes = csr_workspace_bytes(V, E);
-    size_t a = 0;
-    cub::DeviceRadixSort::SortPairs(nullptr, a, (unsigned long long*)nullptr, (unsigned long long*)nullptr,
-                                    (uint32_t*)nullptr, (uint32_t*)nullptr, (int64_t)V, 0, 64);
-    w.cub_bytes = a;
+    w.tmp_bytes = sort_temp_bytes(V);
     size_t off = align_up(w.csr_bytes, 256);  // the CSR builder's workspace first: its header is the status word
     auto take = [&](size_t bytes) {
         const size_t r = off;
@@ -350,7 +336,7 @@ LayoutWs layout_ws(uint32_t V, uint32_t E) {
     w.off_kout = take(8ull * V);
     w.off_vin = take(4ull * V);
     w.off_vout = take(4ull * V);
-    w.off_cub = take(w.cub_bytes);
+    w.off_tmp = take(w.tmp_bytes);
     w.off_src = take(4ull * E);
     w.off_dst = take(4ull * E);
     w.off_eout = take(4);
@@ -385,10 +371,9 @@ sssp_status layout_build(const sssp_graph* g, uint32_t* row_ptr_out, uint32_t* c
     }
     k_lay_keys<<<gv, 256, 0, st>>>(g->V, B, deg, kin, vin);
     CK(cudaGetLastError());
-    size_t tb = L.cub_bytes;
-    CK(cub::DeviceRadixSort::SortPairs(p + L.off_cub, tb, kin, kout, vin, vout, (int64_t)g->V, 0,
-                                       32 + (int)bits_for(g->partitions - 1u), st));
-    k_lay_slots<<<gv, 256, 0, st>>>(g->V, vout, ids_out, slots_out);
+    bool second = false;
+    CK(sort_pairs_u64(p + L.off_tmp, kin, kout, vin, vout, g->V, 32 + (int)bits_for(g->partitions - 1u), st, &second));
+    k_lay_slots<<<gv, 256, 0, st>>>(g->V, second ? vout : vin, ids_out, slots_out);
     CK(cudaGetLastError());
     if (g->E) {
         k_lay_coo<<<grid_for((uint64_t)g->V * 32), 256, 0, st>>>(g->V, g->row_ptr, g->col, slots_out, src, dst);
@@ -402,9 +387,7 @@ sssp_status layout_build(const sssp_graph* g, uint32_t* row_ptr_out, uint32_t* c
 
 size_t compact_workspace_bytes(uint32_t V, uint32_t E) {
     (void)V;
-    size_t a = 0;
-    cub::DeviceScan::InclusiveSum(nullptr, a, (uint32_t*)nullptr, (uint32_t*)nullptr, (int64_t)E);
-    return WS_HEADER_BYTES + 2 * align_up(4ull * std::max<uint32_t>(E, 1), 256) + align_up(a, 256);
+    return WS_HEADER_BYTES + 2 * align_up(4ull * std::max<uint32_t>(E, 1), 256) + align_up(scan_temp_bytes(E), 256);
 }
 
 sssp_status compact_launch(const sssp_graph* g, const uint8_t* keep, uint32_t* row_ptr_out, uint32_t* col_out,
@@ -421,9 +404,7 @@ sssp_status compact_launch(const sssp_graph* g, const uint8_t* keep, uint32_t* r
     if (g->E) {
         k_keep_u32<<<gr, 256, 0, st>>>(g->E, keep, flags);
         CK(cudaGetLastError());
-        size_t tb = 0;
-        cub::DeviceScan::InclusiveSum(nullptr, tb, flags, pos, (int64_t)g->E, st);
-        CK(cub::DeviceScan::InclusiveSum(tmp, tb, flags, pos, (int64_t)g->E, st));
+        CK(inclusive_scan_u32(tmp, flags, pos, g->E, st));
     }
     k_compact<<<gr, 256, 0, st>>>(g->V, g->E, g->row_ptr, g->col, static_cast<const uint32_t*>(g->w), keep, pos,
                                   row_ptr_out, col_out, w_out, emap_out, E_out);

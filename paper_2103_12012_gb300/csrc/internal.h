@@ -107,6 +107,15 @@ sssp_status compact_launch(const sssp_graph* g, const uint8_t* keep, uint32_t* r
                            uint32_t* w_out, uint32_t* emap_out, uint32_t* E_out, void* ws, size_t ws_bytes,
                            cudaStream_t st);
 
+// ------------------------------------------------------------------- sort.cu
+// stable LSD radix sort of (key, value) pairs on key bits [0, end_bit), ping-ponging between
+// (k0, v0) and (k1, v1); *in_second tells which pair of buffers holds the result
+size_t sort_temp_bytes(uint64_t n);
+cudaError_t sort_pairs_u64(void* tmp, unsigned long long* k0, unsigned long long* k1, uint32_t* v0, uint32_t* v1,
+                           uint64_t n, int end_bit, cudaStream_t st, bool* in_second);
+size_t scan_temp_bytes(uint64_t n);
+cudaError_t inclusive_scan_u32(void* tmp, const uint32_t* in, uint32_t* out, uint64_t n, cudaStream_t st);
+
 // ------------------------------------------------------------------ prune.cu
 cudaError_t prune_launch(const sssp_graph* g, int mode, uint8_t* keep, uint32_t* witness, cudaStream_t st);
 TrishlaJob trishla_job(const sssp_graph* g, int mode, uint8_t* keep, uint32_t* witness);
