@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--delta", type=float, default=0.0)
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--split", type=int, default=0)
+    ap.add_argument("--policy", type=int, default=0, help="frontier policy (0 relative, 1 fixed, 2 near-far, 3 all)")
+    ap.add_argument("--hubs", type=int, default=0, help="hub_count (layout graphs)")
     ap.add_argument("--no-tune", action="store_true", help="library defaults instead of the autotuned schedule")
     ap.add_argument("--profile-case", choices=["batched", "batched-full", "backward", "prune", "grid", "all"],
                     help="run a small case of one kernel three times and exit (for ncu captures)")
@@ -241,10 +243,11 @@ def run_ours(a):
     sources_d = torch.from_numpy(srcs.view(np.int32)).to(dev)
     tuned_ms = None
     if a.no_tune or a.threads or a.tile or a.delta or a.split:
-        opts = sssp.options(threads=a.threads, tile=a.tile, delta=a.delta, split=a.split)
+        opts = sssp.options(threads=a.threads, tile=a.tile, delta=a.delta, split=a.split, policy=a.policy,
+                            hub_count=a.hubs)
     else:
         t0 = time.perf_counter()
-        opts, tuned_ms = sssp.autotune(h, sources_d)
+        opts, tuned_ms = sssp.autotune(h, sources_d, trials=2)
         tune_s = time.perf_counter() - t0
     solver = sssp.Solver(h, S, opts)
 
@@ -338,7 +341,7 @@ def run_ours(a):
                              "sources and outputs in the generator's ids",
                    "options": {"threads": opts.threads or 512, "tile": opts.tile or 1024,
                                "delta": opts.delta or 4, "split": opts.split or 1,
-                               "policy": sssp.POLICY_NAMES[opts.policy],
+                               "policy": sssp.POLICY_NAMES[opts.policy], "hub_count": opts.hub_count,
                                "autotuned": not (a.no_tune or a.threads or a.tile or a.delta or a.split)}},
         "roofline": {"bound": "hbm", "kernel": "k_solve (persistent relaxation)", "achieved": round(achieved, 1),
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
@@ -393,7 +396,7 @@ def policy_table(sssp, g, src_d, base, E_ref, reps=3):
                 cands = coarse
             for d in cands:
                 solver = sssp.Solver(g, S, sssp.options(threads=base.threads, tile=base.tile, split=base.split,
-                                                        delta=d, policy=pol))
+                                                        delta=d, policy=pol, hub_count=base.hub_count))
                 a0, b0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 a0.record()
                 solver.launch(src_d)
@@ -434,7 +437,7 @@ def message_table(sssp, g, src_d, base, E_ref, sizes=(0, 1, 8, 32), reps=3):
     out = {}
     for k in sizes:
         o = sssp.options(threads=base.threads, tile=base.tile, split=base.split, delta=base.delta,
-                         policy=base.policy, msg_buffer=k)
+                         policy=base.policy, msg_buffer=k, hub_count=base.hub_count)
         solver = sssp.Solver(g, S, o)
         solver.launch(src_d)
         st, stats = solver.status()

@@ -106,7 +106,12 @@ typedef struct {
                               a warp holds its messages and pushes them out, with one release fence,
                               once it holds k of them (size criterion) and at the end of every
                               sub-round (age criterion).  Messages inside a unit are never held. */
-    uint32_t reserved;     /* must be 0 */
+    uint32_t hub_count;    /* on a graph from sssp_layout (vertices stored by degree, highest first, inside
+                              each partition): the first hub_count stored vertices of every partition
+                              are hubs, which a round of sssp_solve takes only while their distance is
+                              within delta / 4 of the unit's minimum (0 = no hubs; ignored on other
+                              graphs).  Processing a hub twice costs its whole row, so hubs wait for a
+                              narrower bucket while the other vertices may take a wider one. */
     void* ev_relax_begin;  /* cudaEvent_t or NULL: recorded on `stream` right before the relaxation kernel */
     void* ev_relax_end;    /* cudaEvent_t or NULL: recorded right after it (for timing that kernel alone) */
 } sssp_options;
@@ -307,9 +312,12 @@ sssp_status sssp_update(const sssp_graph* g, uint32_t S, void* dist, uint32_t* p
  * candidate schedules and returns the fastest: for each frontier policy
  * RELATIVE, FIXED and NEAR_FAR the bucket width delta is searched over
  * {1/64 .. 4} x the mean of a sample of the weights (powers of two), and ALL
- * once; the best is refined at 3/4 and 3/2 of its delta, then tile over
- * {1024, 2048, 4096}, then split over {1, 2, 4} (split only where ws is large
- * enough).  The base options' policy is ignored.  Each candidate runs `trials` times (>= 1) after one
+ * once; the best is refined at 3/4 and 3/2 of its delta; on a layout graph
+ * hub_count over {256, 512, 1024} is tried with 1, 1.5, 2 and 3 times that
+ * delta under RELATIVE, FIXED and NEAR_FAR; then tile over {1024, 2048, 4096},
+ * then split over {1, 2, 4} (split
+ * only where ws is large enough).  The base options' policy and hub_count are
+ * ignored.  Each candidate runs `trials` times (>= 1) after one
  * warm-up, timed with CUDA events on `stream`; candidates that fail are
  * skipped.  Synchronous.  Results do not depend on the schedule, so dist and
  * pred hold a valid solve afterwards.

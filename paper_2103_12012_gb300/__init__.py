@@ -39,7 +39,7 @@ class SsspGraph(ctypes.Structure):
 class SsspOptions(ctypes.Structure):
     _fields_ = [("threads", u32), ("blocks_per_sm", u32), ("tile", u32), ("split", u32),
                 ("delta", ctypes.c_double), ("timeout_ns", u64), ("flags", u32), ("policy", u32),
-                ("msg_buffer", u32), ("reserved", u32), ("ev_relax_begin", P), ("ev_relax_end", P)]
+                ("msg_buffer", u32), ("hub_count", u32), ("ev_relax_begin", P), ("ev_relax_end", P)]
 
 
 class SsspStats(ctypes.Structure):
@@ -143,9 +143,9 @@ def _ws(nbytes):
 
 
 def options(threads=0, blocks_per_sm=0, tile=0, split=0, delta=0.0, timeout_ns=0, flags=0,
-            policy=POLICY_RELATIVE, msg_buffer=0) -> SsspOptions:
+            policy=POLICY_RELATIVE, msg_buffer=0, hub_count=0) -> SsspOptions:
     return SsspOptions(threads, blocks_per_sm, tile, split, float(delta), int(timeout_ns), flags, int(policy),
-                       int(msg_buffer), 0, None, None)
+                       int(msg_buffer), int(hub_count), None, None)
 
 
 @dataclass
@@ -373,10 +373,10 @@ def autotune(g: DeviceGraph, sources, base: SsspOptions | None = None, trials: i
                 db = json.load(f)
         except ValueError:
             db = {}
-    if key in db and "policy" in db[key]:
+    if key in db and "hub_count" in db[key]:
         o = db[key]
         return options(threads=o["threads"], tile=o["tile"], split=o["split"], delta=o["delta"],
-                       policy=o["policy"]), None
+                       policy=o["policy"], hub_count=o["hub_count"]), None
     solver = Solver(g, S, options(split=4))  # workspace large enough for every split candidate
     if isinstance(sources, np.ndarray) or isinstance(sources, (list, tuple)):
         sources = _as_dev_u32(np.asarray(sources, np.uint32))
@@ -387,7 +387,7 @@ def autotune(g: DeviceGraph, sources, base: SsspOptions | None = None, trials: i
                                _ptr(solver.ws), solver.ws_bytes, ctypes.byref(b), trials, ctypes.byref(best),
                                ctypes.byref(ms), _stream()), "sssp_autotune")
     rec = dict(threads=int(best.threads), tile=int(best.tile), split=int(best.split), delta=float(best.delta),
-               policy=int(best.policy), ms=round(float(ms.value), 4))
+               policy=int(best.policy), hub_count=int(best.hub_count), ms=round(float(ms.value), 4))
     if cache:
         db[key] = rec
         os.makedirs(os.path.dirname(path), exist_ok=True)
@@ -396,7 +396,7 @@ def autotune(g: DeviceGraph, sources, base: SsspOptions | None = None, trials: i
             json.dump(db, f, indent=1, sort_keys=True)
         os.replace(tmp, path)
     return options(threads=rec["threads"], tile=rec["tile"], split=rec["split"], delta=rec["delta"],
-                   policy=rec["policy"]), rec["ms"]
+                   policy=rec["policy"], hub_count=rec["hub_count"]), rec["ms"]
 
 
 def solve(g: DeviceGraph, sources, opts: SsspOptions | None = None, check=True):

@@ -25,7 +25,7 @@ constexpr float DEF_DELTA_F32 = 0.0625f;
 
 struct Resolved {
     uint32_t threads, tile, split, bps;
-    uint32_t delta_bits, policy, msg_buffer;
+    uint32_t delta_bits, policy, msg_buffer, hub_count, hub_delta_bits;
     uint64_t timeout_ns;
     uint32_t flags;
     cudaEvent_t ev_begin, ev_end;
@@ -50,6 +50,19 @@ uint32_t delta_bits_for(int wtype, double delta) {
     return (uint32_t)std::min(4294967294.0, std::max(1.0, std::floor(delta)));
 }
 
+// bucket width of hubs: a quarter of the round's (at least one unit for uint32 distances)
+uint32_t hub_delta_bits_for(int wtype, uint32_t delta_bits) {
+    if (wtype == SSSP_W_F32) {
+        float f;
+        std::memcpy(&f, &delta_bits, 4);
+        f *= 0.25f;
+        uint32_t b;
+        std::memcpy(&b, &f, 4);
+        return b;
+    }
+    return std::max(1u, delta_bits >> 2);
+}
+
 bool resolve(const sssp_options* o, int wtype, Resolved* r) {
     sssp_options d{};
     if (!o) o = &d;
@@ -62,13 +75,15 @@ bool resolve(const sssp_options* o, int wtype, Resolved* r) {
     r->flags = o->flags;
     r->policy = o->policy;
     r->msg_buffer = o->msg_buffer;
+    r->hub_count = o->hub_count;
+    r->hub_delta_bits = hub_delta_bits_for(wtype, r->delta_bits);
     r->ev_begin = static_cast<cudaEvent_t>(o->ev_relax_begin);
     r->ev_end = static_cast<cudaEvent_t>(o->ev_relax_end);
     if (r->threads < 128 || r->threads > 1024 || (r->threads % 32)) return false;
     if (r->tile < 32 || r->tile > 4096) return false;
     if (r->split > 1024) return false;
     if (r->policy > SSSP_POLICY_ALL) return false;
-    if (r->msg_buffer > 32 || o->reserved != 0) return false;
+    if (r->msg_buffer > 32) return false;
     if (!(o->delta >= 0.0) || std::isinf(o->delta)) return false;
     return true;
 }
@@ -228,6 +243,8 @@ static sssp_status solve_impl(const sssp_graph* g, const uint32_t* sources, uint
     l.delta_bits = r.delta_bits;
     l.policy = r.policy;
     l.msg_buffer = r.msg_buffer;
+    l.hub_count = g->ids ? std::min(r.hub_count, L.B) : 0u;  // layout graphs only
+    l.hub_delta_bits = r.hub_delta_bits;
     l.timeout_ns = r.timeout_ns;
     l.hold_pending = (r.flags & SSSP_FLAG_TEST_HOLD_PENDING) ? 1u : 0u;
     l.ev_begin = r.ev_begin;
@@ -342,6 +359,26 @@ sssp_status sssp_autotune(const sssp_graph* g, const uint32_t* sources, uint32_t
         if (ms < cur_ms) {
             cur_ms = ms;
             cur = o;
+        }
+    }
+    // on a layout graph: hubs (the highest-degree stored vertices of each partition) on a quarter of
+    // the width, and the other vertices on a wider bucket than the best without hubs
+    if (g->ids) {
+        const sssp_options nohub = cur;
+        for (uint32_t pol : {(uint32_t)SSSP_POLICY_RELATIVE, (uint32_t)SSSP_POLICY_FIXED, (uint32_t)SSSP_POLICY_NEAR_FAR}) {
+            for (uint32_t hubs : {256u, 512u, 1024u}) {
+                for (double f : {1.0, 1.5, 2.0, 3.0}) {
+                    sssp_options o = nohub;
+                    o.policy = pol;
+                    o.hub_count = hubs;
+                    o.delta = g->wtype == SSSP_W_F32 ? nohub.delta * f : std::max(1.0, std::floor(nohub.delta * f));
+                    const float ms = run(o);
+                    if (ms < cur_ms) {
+                        cur_ms = ms;
+                        cur = o;
+                    }
+                }
+            }
         }
     }
     for (uint32_t tile : {1024u, 2048u, 4096u}) {

@@ -247,6 +247,7 @@ struct Ctx {
     uint32_t delta, tile, gcap;
     uint32_t policy;  // SSSP_POLICY_* (static mode; the batched kernel has its own buckets)
     uint32_t msg_buffer;  // 0: direct messages; k: a warp pushes its held messages out at k (static mode)
+    uint32_t hub_count, hub_delta;  // static mode, layout graphs: hubs per partition and their bucket width
     // static-ownership mode only
     uint32_t* dirty;  // this source's unit doorbells
     uint32_t* nf;     // this source's near-far split point per unit (owner block only)
@@ -322,6 +323,11 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
     __syncthreads();
 
     uint32_t found = 0, nsel = 0, te = 0, thr = 0, bkb = 0;
+    // Hubs (on a layout graph the first hub_count stored vertices of each partition: its
+    // highest-degree ones) are taken only below thr_hub, a narrower bound than thr: a hub
+    // processed before its distance settles is processed again, and that costs its whole row.
+    uint32_t thr_hub = 0;
+    auto lim = [&](uint32_t v) { return (STATIC && v - (v / c.B) * c.B < c.hub_count) ? thr_hub : thr; };
     if constexpr (BK) {
         // ---- Distance buckets (batched: one block owns the whole problem, so every
         // producer is this block), a two-level radix structure: a vertex is queued in the
@@ -528,6 +534,7 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
         found = sc.cnt;
         if (found != 0) {
             thr = policy_bound<W>(sc.dmin, c.delta, c.policy, sc.nf);
+            thr_hub = min(thr, bucket_bound<W>(sc.dmin, c.hub_delta));
             // near-far: the near set ran dry below the split, so the split moves up
             if (STATIC && tid == 0 && c.policy == SSSP_POLICY_NEAR_FAR && sc.dmin >= sc.nf) c.nf[my_q] = thr;
             const uint32_t nkept = sc.nlist;
@@ -537,7 +544,7 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
             // inbox again
             if (nkept <= c.gcap) {
                 for (uint32_t i = tid; i < nkept + lane; i += T) {  // warp-uniform trip count
-                    const bool take = i < nkept && sm.list_d[i] < thr;
+                    const bool take = i < nkept && sm.list_d[i] < lim(sm.list_v[i]);
                     warp_append(take, take ? sm.list_v[i] : 0u, sm.sel_v, &sc.nsel, c.tile, lane);
                 }
             } else {
@@ -556,7 +563,7 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
                             ds[g] = i0 + 32u * g < total ? (uint32_t)(__ldcg(&c.packed[vs[g]]) >> 32) : 0xFFFFFFFFu;
 #pragma unroll
                         for (int g = 0; g < GATHER_G; ++g)
-                            warp_append(ds[g] < thr, vs[g], sm.sel_v, &sc.nsel, c.tile, lane);
+                            warp_append(ds[g] < lim(vs[g]), vs[g], sm.sel_v, &sc.nsel, c.tile, lane);
                     }
                 }
             }
@@ -643,10 +650,10 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
             // EDGE_BATCH edges in flight together: all CSR loads, then all read-first
             // filters, then all atomics.  Its edges are a block-width apart (lanes read
             // consecutive edges: coalesced across short rows) unless the taken vertices
-            // average 32 edges or more (hubs), where a thread takes consecutive edges and
-            // one search of the degree prefix serves all of them.  Row of edge k: the
-            // largest a < nsel with sel_pref[a] <= k (binary lifting, the batch's
-            // searches interleaved).
+            // average 32 edges or more (hubs), where a warp takes consecutive edges, its lane
+            // l the ones 32 apart, and one search of the degree prefix serves the lane's
+            // batch.  Row of edge k: the largest a < nsel with sel_pref[a] <= k (binary
+            // lifting, the batch's searches interleaved).
             uint32_t lact = 0, bad = 0;
             uint32_t n_ai = 0, n_rem = 0;  // statistics: atomics | improved << 16, remote activations
             const bool consec = te >= 32u * nsel;
@@ -655,7 +662,10 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
             // the filter there while this block's relaxations mostly reach the atomic (at
             // least one atomic per four edges so far: wavefront graphs such as grids).
             const bool filt = BK || te > T || sm.st[ST_ATOMICS] * 4u < sm.st[ST_EDGES];
-            const uint32_t kstep = consec ? 1u : T;
+            // consecutive mode: a warp takes 32 * EDGE_BATCH consecutive edges and lane l edges
+            // l, l + 32, ... of them, so every load instruction reads 32 consecutive words (lane l
+            // taking 3 adjacent edges spreads each load over 384 bytes: 1.5% slower on R-MAT)
+            const uint32_t kstep = consec ? 32u : T;
             const uint32_t top = nsel > 1u ? 1u << (31 - __clz(nsel - 1u)) : 0u;
             // A sub-round of at most one edge per thread is a chain of dependent global
             // accesses.  There thread k takes edge k, and a vertex of this unit that it
@@ -678,7 +688,7 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
                         bad |= 2u;
                     } else {
                         const bool mine = !last && v >= lo && v < hi &&
-                                          (BK ? W::bucket(cand, c.delta) == bkb : cand < thr);
+                                          (BK ? W::bucket(cand, c.delta) == bkb : cand < lim(v));
                         uint32_t beg = 0, end = 0, lab = v;
                         if (mine) {
                             beg = __ldg(&c.row_ptr[v]);
@@ -722,7 +732,7 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
                 // with held messages the warp's lanes stay together (ballots): the trip count follows
                 // lane 0's first edge, and lanes past the end carry no edge
                 const uint32_t kwarp0 = consec ? (tid & ~31u) * EDGE_BATCH : (tid & ~31u);
-                for (uint32_t k0 = consec ? tid * EDGE_BATCH : tid, kw = kwarp0; (held ? kw : k0) < te;
+                for (uint32_t k0 = consec ? (tid & ~31u) * EDGE_BATCH + lane : tid, kw = kwarp0; (held ? kw : k0) < te;
                      k0 += EDGE_BATCH * T, kw += EDGE_BATCH * T) {
                     uint32_t vv[EDGE_BATCH], cc[EDGE_BATCH], aa[EDGE_BATCH];
     #pragma unroll
@@ -733,7 +743,7 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
     #pragma unroll
                         for (int j = 1; j < EDGE_BATCH; ++j) {  // step over row ends; sel_pref[nsel] = te
                             uint32_t a = aa[j - 1];
-                            while (a + 1u < nsel && sm.sel_pref[a + 1u] <= k0 + (uint32_t)j) ++a;
+                            while (a + 1u < nsel && sm.sel_pref[a + 1u] <= k0 + (uint32_t)j * kstep) ++a;
                             aa[j] = a;
                         }
                     } else {
@@ -785,7 +795,7 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
                             if (key < old && (uint32_t)(old >> 32) > cc[j]) {
                                 n_ai += 1u << 16;
                                 // near and in this unit: relax it in the next sub-round
-                                const bool near = BK ? W::bucket(cc[j], c.delta) == bkb : cc[j] < thr;
+                                const bool near = BK ? W::bucket(cc[j], c.delta) == bkb : cc[j] < lim(vv[j]);
                                 if (!last && vv[j] >= lo && vv[j] < hi && near) {
                                     const uint32_t pos = atomicAdd(&sc.nlq[sub & 1u], 1u);
                                     if (pos < c.tile) {
@@ -1073,6 +1083,8 @@ __global__ void __launch_bounds__(SOLVE_MAX_THREADS, 4) k_solve(SolveLaunch L) {
     c.gcap = gather_cap(L.tile);
     c.policy = L.policy;
     c.msg_buffer = L.msg_buffer;
+    c.hub_count = L.hub_count;
+    c.hub_delta = L.hub_delta_bits;
     c.B = L.B;
     c.Bq = L.Bq;
     c.split = L.split;
@@ -1208,6 +1220,8 @@ __global__ void __launch_bounds__(SOLVE_MAX_THREADS, 4) k_batched(BatchLaunch L)
     c.nf = nullptr;
     c.policy = SSSP_POLICY_RELATIVE;
     c.msg_buffer = 0;
+    c.hub_count = 0;
+    c.hub_delta = 0;
     c.ids = nullptr;
     c.B = c.Bq = c.split = 1u;
     c.Qw = 0;

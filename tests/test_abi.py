@@ -154,10 +154,10 @@ def test_no_gpu_means_no_solve():
 
 def test_options_layout_matches_the_header():
     """sssp_options as the header declares it: 4 uint32, a double, a uint64, flags, policy, msg_buffer,
-    a reserved word, two pointers."""
+    hub_count, two pointers."""
     O = sssp.SsspOptions
     assert [f[0] for f in O._fields_] == ["threads", "blocks_per_sm", "tile", "split", "delta", "timeout_ns",
-                                          "flags", "policy", "msg_buffer", "reserved", "ev_relax_begin",
+                                          "flags", "policy", "msg_buffer", "hub_count", "ev_relax_begin",
                                           "ev_relax_end"]
     assert O.delta.offset == 16 and O.timeout_ns.offset == 24 and O.policy.offset == 36
     assert O.msg_buffer.offset == 40 and O.ev_relax_begin.offset == 48 and ctypes.sizeof(O) == 64

@@ -88,7 +88,7 @@ def bench_options(sssp, g, srcs, monkeypatch, tmp_path):
     """The schedule the benchmark times: the autotuner's choice for this graph and these sources
     (a fresh cache, as on a fresh machine)."""
     monkeypatch.setenv("SSSP_TUNE_CACHE", str(tmp_path / "tune.json"))
-    opts, ms = sssp.autotune(g, srcs)
+    opts, ms = sssp.autotune(g, srcs, trials=2)
     assert ms is not None
     return opts
 

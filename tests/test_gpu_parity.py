@@ -251,6 +251,23 @@ def test_solve_partition_counts(sssp, P, split, f32, policy):
     check_solve(sssp, g, ref, [0, 4999, 2500, 0], sssp.options(split=split, policy=policy, delta=delta))
 
 
+@pytest.mark.parametrize("f32", [False, True])
+@pytest.mark.parametrize("policy", [0, 1, 2, 3])
+def test_hubs_wait_for_a_narrower_bucket(sssp, f32, policy):
+    """hub_count on a layout graph (the first hub_count stored vertices of each partition take a
+    quarter-width bucket): exact for every policy, for 1 hub, some, and more than a partition
+    holds; on a graph in the caller's ids the option is ignored."""
+    g0 = gg.rmat(gg.BASE_SEED + 630, 14, 16 << 14, wf32=(0.5, 2.0, 1e-4) if f32 else None)
+    ref = oracle.csr_of(g0)
+    g = sssp.build_csr(g0.V, g0.src, g0.dst, g0.w, partitions=16)
+    h = sssp.layout(g)
+    srcs = gg.pick_sources(gg.BASE_SEED + 630, g0, 4).tolist()
+    delta = 0.5 if f32 else 24
+    for hubs in (1, 64, 100000):
+        check_solve(sssp, h, ref, srcs, sssp.options(policy=policy, delta=delta, hub_count=hubs, split=2))
+    check_solve(sssp, g, ref, srcs, sssp.options(policy=policy, delta=delta, hub_count=64))
+
+
 @pytest.mark.parametrize("msg", [1, 8, 32])
 @pytest.mark.parametrize("P,split", [(7, 1), (148, 1), (37, 3)])
 @pytest.mark.parametrize("f32", [False, True])
