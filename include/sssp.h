@@ -109,8 +109,9 @@ typedef struct {
     uint32_t hub_count;    /* on a graph from sssp_layout (vertices stored by degree, highest first, inside
                               each partition): the first hub_count stored vertices of every partition
                               are hubs, which a round of sssp_solve takes only while their distance is
-                              within delta / 4 of the unit's minimum (0 = no hubs; ignored on other
-                              graphs).  Processing a hub twice costs its whole row, so hubs wait for a
+                              within delta / 4 of the unit's minimum, and the next 3 * hub_count
+                              within delta / 2 (0 = no hubs; ignored on other graphs).  Processing a
+                              high-degree vertex twice costs its whole row, so these wait for a
                               narrower bucket while the other vertices may take a wider one. */
     void* ev_relax_begin;  /* cudaEvent_t or NULL: recorded on `stream` right before the relaxation kernel */
     void* ev_relax_end;    /* cudaEvent_t or NULL: recorded right after it (for timing that kernel alone) */

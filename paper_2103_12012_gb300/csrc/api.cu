@@ -25,7 +25,7 @@ constexpr float DEF_DELTA_F32 = 0.0625f;
 
 struct Resolved {
     uint32_t threads, tile, split, bps;
-    uint32_t delta_bits, policy, msg_buffer, hub_count, hub_delta_bits;
+    uint32_t delta_bits, policy, msg_buffer, hub_count, hub_delta_bits, hub_mid_bits;
     uint64_t timeout_ns;
     uint32_t flags;
     cudaEvent_t ev_begin, ev_end;
@@ -50,17 +50,17 @@ uint32_t delta_bits_for(int wtype, double delta) {
     return (uint32_t)std::min(4294967294.0, std::max(1.0, std::floor(delta)));
 }
 
-// bucket width of hubs: a quarter of the round's (at least one unit for uint32 distances)
-uint32_t hub_delta_bits_for(int wtype, uint32_t delta_bits) {
+// bucket width of hubs: the round's over 2^shift (at least one unit for uint32 distances)
+uint32_t hub_delta_bits_for(int wtype, uint32_t delta_bits, int shift) {
     if (wtype == SSSP_W_F32) {
         float f;
         std::memcpy(&f, &delta_bits, 4);
-        f *= 0.25f;
+        f = std::ldexp(f, -shift);
         uint32_t b;
         std::memcpy(&b, &f, 4);
         return b;
     }
-    return std::max(1u, delta_bits >> 2);
+    return std::max(1u, delta_bits >> shift);
 }
 
 bool resolve(const sssp_options* o, int wtype, Resolved* r) {
@@ -76,7 +76,8 @@ bool resolve(const sssp_options* o, int wtype, Resolved* r) {
     r->policy = o->policy;
     r->msg_buffer = o->msg_buffer;
     r->hub_count = o->hub_count;
-    r->hub_delta_bits = hub_delta_bits_for(wtype, r->delta_bits);
+    r->hub_delta_bits = hub_delta_bits_for(wtype, r->delta_bits, 2);
+    r->hub_mid_bits = hub_delta_bits_for(wtype, r->delta_bits, 1);
     r->ev_begin = static_cast<cudaEvent_t>(o->ev_relax_begin);
     r->ev_end = static_cast<cudaEvent_t>(o->ev_relax_end);
     if (r->threads < 128 || r->threads > 1024 || (r->threads % 32)) return false;
@@ -245,6 +246,7 @@ static sssp_status solve_impl(const sssp_graph* g, const uint32_t* sources, uint
     l.msg_buffer = r.msg_buffer;
     l.hub_count = g->ids ? std::min(r.hub_count, L.B) : 0u;  // layout graphs only
     l.hub_delta_bits = r.hub_delta_bits;
+    l.hub_mid_bits = r.hub_mid_bits;
     l.timeout_ns = r.timeout_ns;
     l.hold_pending = (r.flags & SSSP_FLAG_TEST_HOLD_PENDING) ? 1u : 0u;
     l.ev_begin = r.ev_begin;

@@ -43,7 +43,8 @@ struct SolveLaunch {
     uint32_t policy;      // SSSP_POLICY_*
     uint32_t msg_buffer;  // 0: direct messages, else the push-out size
     uint32_t hub_count;   // layout graphs: the first hub_count stored vertices of each partition are hubs
-    uint32_t hub_delta_bits;  // bucket width of hubs
+    uint32_t hub_delta_bits;  // bucket width of hubs (a quarter of delta)
+    uint32_t hub_mid_bits;    // bucket width of the next 3 * hub_count vertices (half of delta)
     uint64_t timeout_ns;
     uint32_t hold_pending;
     cudaEvent_t ev_begin, ev_end;  // optional timing events around the relaxation kernel

@@ -247,7 +247,7 @@ struct Ctx {
     uint32_t delta, tile, gcap;
     uint32_t policy;  // SSSP_POLICY_* (static mode; the batched kernel has its own buckets)
     uint32_t msg_buffer;  // 0: direct messages; k: a warp pushes its held messages out at k (static mode)
-    uint32_t hub_count, hub_delta;  // static mode, layout graphs: hubs per partition and their bucket width
+    uint32_t hub_count, hub_delta, hub_mid;  // static mode, layout graphs: hubs per partition, bucket widths
     // static-ownership mode only
     uint32_t* dirty;  // this source's unit doorbells
     uint32_t* nf;     // this source's near-far split point per unit (owner block only)
@@ -324,10 +324,15 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
 
     uint32_t found = 0, nsel = 0, te = 0, thr = 0, bkb = 0;
     // Hubs (on a layout graph the first hub_count stored vertices of each partition: its
-    // highest-degree ones) are taken only below thr_hub, a narrower bound than thr: a hub
-    // processed before its distance settles is processed again, and that costs its whole row.
-    uint32_t thr_hub = 0;
-    auto lim = [&](uint32_t v) { return (STATIC && v - (v / c.B) * c.B < c.hub_count) ? thr_hub : thr; };
+    // highest-degree ones) are taken only below thr_hub, a bucket of a quarter of the width,
+    // and the next 3 * hub_count only below thr_mid, half of it: a vertex processed before its
+    // distance settles is processed again, and for these that costs long rows.
+    uint32_t thr_hub = 0, thr_mid = 0;
+    auto lim = [&](uint32_t v) {
+        if (!STATIC) return thr;
+        const uint32_t off = v - (v / c.B) * c.B;
+        return off < c.hub_count ? thr_hub : off < 4u * c.hub_count ? thr_mid : thr;
+    };
     if constexpr (BK) {
         // ---- Distance buckets (batched: one block owns the whole problem, so every
         // producer is this block), a two-level radix structure: a vertex is queued in the
@@ -535,6 +540,7 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
         if (found != 0) {
             thr = policy_bound<W>(sc.dmin, c.delta, c.policy, sc.nf);
             thr_hub = min(thr, bucket_bound<W>(sc.dmin, c.hub_delta));
+            thr_mid = min(thr, bucket_bound<W>(sc.dmin, c.hub_mid));
             // near-far: the near set ran dry below the split, so the split moves up
             if (STATIC && tid == 0 && c.policy == SSSP_POLICY_NEAR_FAR && sc.dmin >= sc.nf) c.nf[my_q] = thr;
             const uint32_t nkept = sc.nlist;
@@ -1085,6 +1091,7 @@ __global__ void __launch_bounds__(SOLVE_MAX_THREADS, 4) k_solve(SolveLaunch L) {
     c.msg_buffer = L.msg_buffer;
     c.hub_count = L.hub_count;
     c.hub_delta = L.hub_delta_bits;
+    c.hub_mid = L.hub_mid_bits;
     c.B = L.B;
     c.Bq = L.Bq;
     c.split = L.split;
@@ -1222,6 +1229,7 @@ __global__ void __launch_bounds__(SOLVE_MAX_THREADS, 4) k_batched(BatchLaunch L)
     c.msg_buffer = 0;
     c.hub_count = 0;
     c.hub_delta = 0;
+    c.hub_mid = 0;
     c.ids = nullptr;
     c.B = c.Bq = c.split = 1u;
     c.Qw = 0;

@@ -255,8 +255,9 @@ def test_solve_partition_counts(sssp, P, split, f32, policy):
 @pytest.mark.parametrize("policy", [0, 1, 2, 3])
 def test_hubs_wait_for_a_narrower_bucket(sssp, f32, policy):
     """hub_count on a layout graph (the first hub_count stored vertices of each partition take a
-    quarter-width bucket): exact for every policy, for 1 hub, some, and more than a partition
-    holds; on a graph in the caller's ids the option is ignored."""
+    quarter-width bucket, the next 3 * hub_count a half-width one): exact for every policy, for 1
+    hub, some, and more than a partition holds; on a graph in the caller's ids the option is
+    ignored."""
     g0 = gg.rmat(gg.BASE_SEED + 630, 14, 16 << 14, wf32=(0.5, 2.0, 1e-4) if f32 else None)
     ref = oracle.csr_of(g0)
     g = sssp.build_csr(g0.V, g0.src, g0.dst, g0.w, partitions=16)
