@@ -873,7 +873,7 @@ def _reduce_sharded(name, d, world, dev):
     dist.all_reduce(mx, op=dist.ReduceOp.MAX)
     dist.all_reduce(sm, op=dist.ReduceOp.SUM)
     out = dict(d)
-    if any(np.isnan(t.tolist())) or "error" in d:
+    if any(np.isnan(sm.tolist())) or "error" in d:  # a NaN from any rank survives the SUM
         out["error"] = out.get("error", "an extra failed on another rank")
         return out
     for i, k in enumerate(keys):

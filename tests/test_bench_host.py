@@ -71,3 +71,50 @@ def test_cpu_baseline_single_all_cores_and_trishla():
     assert ac["cores"] == min(4, os.cpu_count() or 1) and ac["value"] > 0 and ac["unit"] == out["unit"]
     tr = out["trishla_er16k"]
     assert tr["edges"] == 131072 and tr["pruned"] > 0 and tr["s"] > 0
+
+
+def test_tree_path_sums_and_depth_against_brute_force():
+    """The grid latency model's hop and crossing counts: per-vertex sums along predecessor paths
+    by pointer doubling, against walking each path."""
+    import numpy as np
+    import torch
+    NONE = 0xFFFFFFFF
+    rng = np.random.default_rng(5)
+    for n in (1, 2, 7, 300):
+        for _ in range(4):
+            order = rng.permutation(n)
+            pred = np.full(n, NONE, np.uint32)
+            for k in range(1, n):
+                if rng.random() < 0.9:
+                    pred[order[k]] = order[rng.integers(0, k)]
+            w = rng.integers(0, 2, n)
+            got = bench.tree_path_sums(torch.from_numpy(pred.view(np.int32)[None]), torch.from_numpy(w)[None])[0]
+            hops = bench.tree_path_sums(torch.from_numpy(pred.view(np.int32)[None]))[0]
+            for v in range(n):
+                s = h = 0
+                x = v
+                while pred[x] != NONE:
+                    s += int(w[x])
+                    h += 1
+                    x = pred[x]
+                assert int(got[v]) == s and int(hops[v]) == h
+            assert int(bench.tree_depth(torch.from_numpy(pred.view(np.int32)[None]))[0]) == int(hops.max())
+    chain = np.concatenate([np.array([NONE], np.uint32), np.arange(99999, dtype=np.uint32)])
+    assert int(bench.tree_depth(torch.from_numpy(chain.view(np.int32)[None]))[0]) == 99999
+
+
+def test_batched_traffic_lookup(tmp_path, monkeypatch):
+    src = tmp_path / "k.cu"
+    src.write_text("__global__ void k() {}\n")
+    (tmp_path / "profiles").mkdir()
+    rec = {"source": "k.cu", "code_sha256": bench.code_sha256(str(src)), "dram_bytes_per_scanned_edge": 121.5}
+    (tmp_path / "profiles" / "k_batched_dram_traffic.txt").write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.batched_traffic(1000) == 121500
+    src.write_text("__global__ void k() { int changed = 1; }\n")
+    assert bench.batched_traffic(1000) is None
+
+
+def test_sharded_extras_pass_through_on_one_rank():
+    d = {"graph_replay_ms": 47.2, "problems": 8192}
+    assert bench._reduce_sharded("batched", d, 1, None) is d

@@ -142,3 +142,32 @@ def test_planner_assignments():
     assert sssp.shard_sources(8, 1, 3).tolist() == [1, 4, 7]
     with pytest.raises(sssp.SsspError):
         sssp.shard_problems([1, 2], 0)
+
+
+def _reduce_worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    b = {"graph_replay_ms": 40.0 + rank, "per_graph_launches_ms": 400.0, "per_problem_launches_ms": 4000.0 + rank,
+         "problems": 4096 + rank, "edges_total": 10 ** 6}
+    d = {"forward_ms": 1.0, "backward_ms": 0.5 + rank, "forward_backward_ms": 1.6, "sources_this_rank": 16}
+    bad = {"error": "boom"} if rank == 1 else dict(d)
+    out[rank] = (bench._reduce_sharded("batched", b, world, "cpu"), bench._reduce_sharded("differentiable", d, world, "cpu"),
+                 bench._reduce_sharded("differentiable", bad, world, "cpu"))
+    dist.destroy_process_group()
+
+
+def test_two_ranks_reduce_the_sharded_extras():
+    """bench.py's reduction of the sharded extras: times by MAX, counts by SUM, rates recomputed
+    from the reduced values; a rank whose extra failed makes every rank report an error (the
+    collectives still match)."""
+    world = 2
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_reduce_worker, args=(world, _free_port(), out), nprocs=world, start_method="spawn", join=True)
+    for r in range(world):
+        b, d, bad = out[r]
+        assert b["graph_replay_ms"] == 41.0 and b["problems"] == 8193 and b["per_problem_launches_ms"] == 4001.0
+        assert b["solves_per_s"] == round(8193 / 41.0 * 1e3, 1) and b["ranks"] == 2
+        assert d["backward_ms"] == 1.5 and d["sources_this_rank"] == 32
+        assert "error" in bad
