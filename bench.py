@@ -704,7 +704,7 @@ def extras_differentiable(sssp, dev, rank=0, world=1):
     # 16 partitions: 512 units for the 32 sources keep the persistent blocks busy
     g = sssp.build_csr(g0.V, g0.src, g0.dst, g0.w, partitions=16)
     src_d = torch.from_numpy(srcs.view(np.int32)).to(dev)
-    opts, _ = sssp.autotune(g, src_d)
+    opts, _ = sssp.autotune(g, src_d, trials=2)
     solver = sssp.Solver(g, len(srcs), opts)
     gup_d = torch.from_numpy(gup).to(dev)
     solver.launch(src_d)
@@ -778,7 +778,7 @@ def extras_grid(sssp, dev):
     g = sssp.build_csr(g0.V, g0.src, g0.dst, g0.w, partitions=P)
     del g0
     src_d = torch.from_numpy(srcs.view(np.int32)).to(dev)
-    opts, _ = sssp.autotune(g, src_d)
+    opts, _ = sssp.autotune(g, src_d, trials=2)
     solver = sssp.Solver(g, 1, opts)
     solver.launch(src_d)
     st, stats = solver.status()
@@ -820,7 +820,7 @@ def extras_warm(sssp, dev):
     g = sssp.layout(sssp.build_csr(g0.V, g0.src, g0.dst, g0.w, partitions=P))
     del g0
     src_d = torch.from_numpy(srcs.view(np.int32)).to(dev)
-    opts, _ = sssp.autotune(g, src_d)
+    opts, _ = sssp.autotune(g, src_d, trials=2)
     rng = np.random.default_rng(gg.BASE_SEED + 40)
     idx = torch.from_numpy(np.sort(rng.choice(g.E, g.E // 1000, replace=False)).astype(np.int64)).to(dev)
     w2 = g.w.clone()
@@ -910,7 +910,7 @@ def extras_prune_overlap(sssp, dev):
         if lay:
             g = sssp.layout(g)
         src_d = torch.from_numpy(np.asarray(srcs, np.uint32).view(np.int32)).to(dev)
-        opts, _ = sssp.autotune(g, src_d)
+        opts, _ = sssp.autotune(g, src_d, trials=2)
         solver = sssp.Solver(g, len(srcs), opts)
         keep = torch.empty(max(g.E, 1), dtype=torch.uint8, device=dev)
         solver.launch_prune(src_d, 0, keep)

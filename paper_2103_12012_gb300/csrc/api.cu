@@ -212,7 +212,9 @@ static sssp_status solve_impl(const sssp_graph* g, const uint32_t* sources, uint
     if (smem > 200 * 1024) return SSSP_EINVAL;
     const bool prune = prune_mode >= 0;
     int per_sm = 0;
-    if (relax_max_blocks_per_sm(g->wtype, r.threads, r.tile, L.Q, &per_sm, prune, r.msg_buffer != 0) != cudaSuccess)
+    const uint32_t hubs = g->ids ? std::min(r.hub_count, L.B) : 0u;  // layout graphs only
+    if (relax_max_blocks_per_sm(g->wtype, r.threads, r.tile, L.Q, &per_sm, prune, r.msg_buffer != 0, hubs != 0) !=
+        cudaSuccess)
         return SSSP_ECUDA;
     if (per_sm <= 0) return SSSP_EUNSUPPORTED;
     if (r.bps) per_sm = std::min<int>(per_sm, (int)r.bps);
@@ -244,7 +246,7 @@ static sssp_status solve_impl(const sssp_graph* g, const uint32_t* sources, uint
     l.delta_bits = r.delta_bits;
     l.policy = r.policy;
     l.msg_buffer = r.msg_buffer;
-    l.hub_count = g->ids ? std::min(r.hub_count, L.B) : 0u;  // layout graphs only
+    l.hub_count = hubs;
     l.hub_delta_bits = r.hub_delta_bits;
     l.hub_mid_bits = r.hub_mid_bits;
     l.timeout_ns = r.timeout_ns;

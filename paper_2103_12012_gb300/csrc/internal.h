@@ -63,7 +63,7 @@ struct SolveLaunch {
 constexpr uint32_t SOLVE_MAX_THREADS = 512;  // block size limit of the solve kernel
 size_t relax_smem_bytes(uint32_t tile, uint32_t Q, bool msgs);
 cudaError_t relax_max_blocks_per_sm(int wtype, uint32_t threads, uint32_t tile, uint32_t Q, int* out,
-                                    bool prune = false, bool msgs = false);
+                                    bool prune = false, bool msgs = false, bool hubs = false);
 cudaError_t launch_solve(const SolveLaunch& L, cudaStream_t st);
 
 // One problem of a batch, in the order blocks take them (largest first).

@@ -302,7 +302,7 @@ __device__ __forceinline__ void bucket_file(const Ctx& c, uint32_t v, uint32_t d
 
 // One round over the unit owning vertices [lo, hi).  Returns the number of
 // queued vertices the scan found (0 = the unit's inbox was empty).
-template <class W, bool STATIC, bool BK, bool HELD = false>
+template <class W, bool STATIC, bool BK, bool HELD = false, bool HUBS = false>
 __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t my_q,
                                 const Smem& sm) {
     static_assert(!(STATIC && BK), "distance buckets belong to the batched kernel");
@@ -327,11 +327,13 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
     // highest-degree ones) are taken only below thr_hub, a bucket of a quarter of the width,
     // and the next 3 * hub_count only below thr_mid, half of it: a vertex processed before its
     // distance settles is processed again, and for these that costs long rows.
-    uint32_t thr_hub = 0, thr_mid = 0;
+    // (the narrower bounds are formed on demand from the round's minimum in shared memory: they are
+    // needed only for candidates and improved targets, and kept in registers they cost spills)
     auto lim = [&](uint32_t v) {
-        if (!STATIC) return thr;
+        if (!HUBS) return thr;
         const uint32_t off = v - (v / c.B) * c.B;
-        return off < c.hub_count ? thr_hub : off < 4u * c.hub_count ? thr_mid : thr;
+        if (off >= 4u * c.hub_count) return thr;
+        return min(thr, bucket_bound<W>(sm.sc->dmin, off < c.hub_count ? c.hub_delta : c.hub_mid));
     };
     if constexpr (BK) {
         // ---- Distance buckets (batched: one block owns the whole problem, so every
@@ -539,8 +541,6 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
         found = sc.cnt;
         if (found != 0) {
             thr = policy_bound<W>(sc.dmin, c.delta, c.policy, sc.nf);
-            thr_hub = min(thr, bucket_bound<W>(sc.dmin, c.hub_delta));
-            thr_mid = min(thr, bucket_bound<W>(sc.dmin, c.hub_mid));
             // near-far: the near set ran dry below the split, so the split moves up
             if (STATIC && tid == 0 && c.policy == SSSP_POLICY_NEAR_FAR && sc.dmin >= sc.nf) c.nf[my_q] = thr;
             const uint32_t nkept = sc.nlist;
@@ -1057,9 +1057,9 @@ __global__ void k_unpack(const unsigned long long* __restrict__ packed, size_t n
 // (each warp one chunk, claimed from the header's cursor) instead of sleeping -- the paper's
 // use of the time processes spend waiting for messages (Sec. III.B) -- and goes back to its
 // doorbells after each; the chunks left when the solve ends are run by a launch after it.
-// HELD: message buffering (msg_buffer > 0), a separate instantiation so that the direct path
-// keeps its registers.
-template <class W, bool PRUNE, bool HELD>
+// HELD: message buffering (msg_buffer > 0); HUBS: hub widths (hub_count > 0 on a layout graph).
+// Separate instantiations, so that the plain path keeps its registers.
+template <class W, bool PRUNE, bool HELD, bool HUBS>
 __global__ void __launch_bounds__(SOLVE_MAX_THREADS, 4) k_solve(SolveLaunch L) {
     extern __shared__ uint32_t dsm[];
     __shared__ uint32_t wsum[32];
@@ -1203,7 +1203,7 @@ __global__ void __launch_bounds__(SOLVE_MAX_THREADS, 4) k_solve(SolveLaunch L) {
         c.bitmap = L.bitmap + (size_t)s * L.words;
         c.dirty = L.dirty + (size_t)s * L.Q;
         c.nf = L.nfsplit + (size_t)s * L.Q;
-        relax_round<W, true, false, HELD>(c, lo, hi, q, sm);
+        relax_round<W, true, false, HELD, HUBS>(c, lo, hi, q, sm);
     }
     __syncthreads();
     flush_stats(L.hdr, sm.st);
@@ -1307,9 +1307,13 @@ cudaError_t set_smem(K kernel, size_t smem) {
 }  // namespace
 
 template <class W>
-const void* solve_kernel(bool prune, bool held) {
-    if (held) return prune ? (const void*)k_solve<W, true, true> : (const void*)k_solve<W, false, true>;
-    return prune ? (const void*)k_solve<W, true, false> : (const void*)k_solve<W, false, false>;
+const void* solve_kernel(bool prune, bool held, bool hubs) {
+    if (hubs) {
+        if (held) return prune ? (const void*)k_solve<W, true, true, true> : (const void*)k_solve<W, false, true, true>;
+        return prune ? (const void*)k_solve<W, true, false, true> : (const void*)k_solve<W, false, false, true>;
+    }
+    if (held) return prune ? (const void*)k_solve<W, true, true, false> : (const void*)k_solve<W, false, true, false>;
+    return prune ? (const void*)k_solve<W, true, false, false> : (const void*)k_solve<W, false, false, false>;
 }
 
 size_t relax_smem_bytes(uint32_t tile, uint32_t Q, bool msgs) {
@@ -1319,9 +1323,9 @@ size_t relax_smem_bytes(uint32_t tile, uint32_t Q, bool msgs) {
 }
 
 cudaError_t relax_max_blocks_per_sm(int wtype, uint32_t threads, uint32_t tile, uint32_t Q, int* out, bool prune,
-                                    bool msgs) {
+                                    bool msgs, bool hubs) {
     const size_t smem = relax_smem_bytes(tile, Q, msgs);
-    const void* k = wtype == SSSP_W_F32 ? solve_kernel<WF32>(prune, msgs) : solve_kernel<WU32>(prune, msgs);
+    const void* k = wtype == SSSP_W_F32 ? solve_kernel<WF32>(prune, msgs, hubs) : solve_kernel<WU32>(prune, msgs, hubs);
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k, (int)threads, smem);
@@ -1363,8 +1367,8 @@ cudaError_t launch_solve(const SolveLaunch& L, cudaStream_t st) {
     void* args[] = {const_cast<SolveLaunch*>(&L)};
     if (L.ev_begin && (e = cudaEventRecord(L.ev_begin, st)) != cudaSuccess) return e;
     {
-        const bool pr = L.prune_on != 0u, held = L.msg_buffer != 0u;
-        const void* k = L.wtype == SSSP_W_F32 ? solve_kernel<WF32>(pr, held) : solve_kernel<WU32>(pr, held);
+        const bool pr = L.prune_on != 0u, held = L.msg_buffer != 0u, hubs = L.hub_count != 0u;
+        const void* k = L.wtype == SSSP_W_F32 ? solve_kernel<WF32>(pr, held, hubs) : solve_kernel<WU32>(pr, held, hubs);
         if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
             return e;
         if ((e = cudaLaunchCooperativeKernel(k, dim3(L.grid), dim3(L.threads), args, smem, st)) != cudaSuccess) return e;
