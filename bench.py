@@ -577,6 +577,36 @@ def cpu_baseline(g0, srcs, all_srcs=None, er16k=True):
         keep, _ = oracle.trishla(r1, P1, 0)
         out["trishla_er16k"] = {"s": round(time.perf_counter() - t0, 4), "cores": 1, "edges": r1.E,
                                 "pruned": int((keep[:r1.E] == 0).sum())}
+        out.update(cpu_other_configs())
+    return out
+
+
+def cpu_other_configs():
+    """The oracle on bounded samples of the batched and differentiable workloads, single-threaded:
+    the first source of every 8th graph of the 512-graph batch (64 problems), and 8 of the 32
+    float32 R-MAT scale-18 sources with the tree gradient of their results."""
+    import oracle
+    out = {}
+    graphs, sources = gg.workload_batch512()
+    t_total, solves = 0.0, 0
+    for gi in range(0, len(graphs), 8):
+        ref = oracle.csr_of(graphs[gi])
+        t0 = time.perf_counter()
+        oracle.dijkstra(ref, int(sources[gi][0]))
+        t_total += time.perf_counter() - t0
+        solves += 1
+    out["batch512_sample"] = {"solves_per_s": round(solves / t_total, 1), "cores": 1, "kind": "oracle",
+                              "sample": f"{solves} problems (first source of every 8th graph), {t_total:.2f} s"}
+    g0, srcs, gup = gg.workload_rmat18_f32()
+    ref = oracle.csr_of(g0)
+    t0 = time.perf_counter()
+    runs = [oracle.dijkstra(ref, int(s)) for s in srcs[:8]]
+    t1 = time.perf_counter()
+    oracle.tree_grad(ref, np.stack([r[0] for r in runs]), np.stack([r[1] for r in runs]), gup[:8])
+    t2 = time.perf_counter()
+    out["rmat18_f32_sample"] = {"forward_ms_per_source": round((t1 - t0) * 1e3 / 8, 2),
+                                "backward_ms_per_source": round((t2 - t1) * 1e3 / 8, 2), "cores": 1,
+                                "kind": "oracle", "sample": "8 of the 32 sources: Dijkstra, then the tree gradient"}
     return out
 
 
