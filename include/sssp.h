@@ -316,7 +316,7 @@ sssp_status sssp_update(const sssp_graph* g, uint32_t S, void* dist, uint32_t* p
  * once; the best is refined at 3/4 and 3/2 of its delta; on a layout graph
  * hub_count over {256, 512, 1024} is tried with 1, 1.5, 2 and 3 times that
  * delta under RELATIVE, FIXED and NEAR_FAR; then tile over {1024, 2048, 4096},
- * then split over {1, 2, 4} (split
+ * then split over {1, 2, 4}, then tile once more if the split changed (split
  * only where ws is large enough).  The base options' policy and hub_count are
  * ignored.  Each candidate runs `trials` times (>= 1) after one
  * warm-up, timed with CUDA events on `stream`; candidates that fail are

@@ -403,6 +403,20 @@ sssp_status sssp_autotune(const sssp_graph* g, const uint32_t* sources, uint32_t
             cur = o;
         }
     }
+    // the tile again at the chosen split (the best tile depends on it: the 4096-square grid takes
+    // 4096 at split 1 but 2048 at split 4)
+    if (cur.split != 1) {
+        for (uint32_t tile : {1024u, 2048u, 4096u}) {
+            if (tile == cur.tile) continue;
+            sssp_options o = cur;
+            o.tile = tile;
+            const float ms = run(o);
+            if (ms < cur_ms) {
+                cur_ms = ms;
+                cur = o;
+            }
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (!(cur_ms < INFINITY)) return SSSP_EINTERNAL;  // no candidate ran
