@@ -269,6 +269,33 @@ def test_hubs_wait_for_a_narrower_bucket(sssp, f32, policy):
     check_solve(sssp, g, ref, srcs, sssp.options(policy=policy, delta=delta, hub_count=64))
 
 
+@pytest.mark.parametrize("prune", [False, True])
+@pytest.mark.parametrize("msg", [0, 8])
+@pytest.mark.parametrize("hubs", [0, 48])
+def test_every_solve_kernel_variant(sssp, prune, msg, hubs):
+    """Each compiled variant of the persistent solve (prune on idle time x held messages x hub
+    widths) on a layout graph, against the oracle; with prune, the keep mask against Algorithm 1."""
+    g0 = gg.rmat(gg.BASE_SEED + 640, 13, 16 << 13)
+    ref = oracle.csr_of(g0)
+    P = 24
+    g = sssp.build_csr(g0.V, g0.src, g0.dst, g0.w, partitions=P)
+    h = sssp.layout(g)
+    srcs = gg.pick_sources(gg.BASE_SEED + 640, g0, 3)
+    o = sssp.options(delta=16, msg_buffer=msg, hub_count=hubs)
+    if prune:
+        dist, pred, keep, wit, st, _ = sssp.solve_prune(h, srcs, 0, o)
+        rk, _ = oracle.trishla(oracle.csr(h.V, np.repeat(np.arange(h.V, dtype=np.uint32),
+                                                          np.diff(u32(h.row_ptr).astype(np.int64))),
+                                          u32(h.col[:h.E]), u32(h.w[:h.E])), P, 0)
+        assert np.array_equal(keep.cpu().numpy(), rk)
+    else:
+        dist, pred, st, _ = sssp.solve(h, srcs, o)
+    assert st == sssp.SSSP_OK
+    for i, s_ in enumerate(srcs):
+        d, p, _ = oracle.dijkstra(ref, int(s_))
+        assert np.array_equal(u32(dist[i]), d) and np.array_equal(u32(pred[i]), p)
+
+
 @pytest.mark.parametrize("msg", [1, 8, 32])
 @pytest.mark.parametrize("P,split", [(7, 1), (148, 1), (37, 3)])
 @pytest.mark.parametrize("f32", [False, True])
