@@ -7,9 +7,11 @@
 //   1. each tile counts its digits (shared atomics) into counts[digit * ntiles + tile];
 //   2. an exclusive prefix sum of counts, digit-major, gives every (digit, tile) the first
 //      output position of its pairs;
-//   3. each tile places its pairs: a warp ranks equal digits within 32 lanes with
-//      __match_any_sync and keeps a running count per digit, warps before it add their digit
-//      counts, so pairs keep their input order within a digit (stable, which LSD needs).
+//   3. each tile orders its pairs by digit in shared memory: a warp ranks equal digits within
+//      32 lanes with __match_any_sync and keeps a running count per digit, warps before it add
+//      their digit counts, so pairs keep their input order within a digit (stable, which LSD
+//      needs); the ordered tile then goes out run by run, consecutive threads storing
+//      consecutive pairs of one digit.
 // Scan: tiles of SCAN_TILE values staged in shared memory; a first kernel sums each tile, the
 // tile sums are scanned (recursively while there are more than one tile of them), and a second
 // kernel scans each tile from its offset.
@@ -35,79 +37,6 @@ constexpr uint32_t SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 __device__ __forceinline__ uint32_t digit_of(unsigned long long k, uint32_t shift) {
     return (uint32_t)(k >> shift) & (RADIX - 1u);
 }
-
-// 1. digit counts of each tile, digit-major
-__global__ void __launch_bounds__(SORT_THREADS) k_sort_count(const unsigned long long* __restrict__ keys,
-                                                             unsigned long long n, uint32_t shift, uint32_t ntiles,
-                                                             uint32_t* counts) {
-    __shared__ uint32_t hist[RADIX];
-    const uint32_t tile = blockIdx.x;
-    hist[threadIdx.x] = 0u;  // SORT_THREADS == RADIX
-    __syncthreads();
-    const unsigned long long base = (unsigned long long)tile * SORT_TILE;
-    for (uint32_t i = threadIdx.x; i < SORT_TILE; i += SORT_THREADS) {
-        const unsigned long long at = base + i;
-        if (at < n) atomicAdd(&hist[digit_of(keys[at], shift)], 1u);
-    }
-    __syncthreads();
-    counts[(size_t)threadIdx.x * ntiles + tile] = hist[threadIdx.x];
-}
-
-// 3. stable placement of each tile's pairs from the scanned counts
-__global__ void __launch_bounds__(SORT_THREADS) k_sort_place(const unsigned long long* __restrict__ kin,
-                                                             const uint32_t* __restrict__ vin, unsigned long long n,
-                                                             uint32_t shift, uint32_t ntiles,
-                                                             const uint32_t* __restrict__ offsets,
-                                                             unsigned long long* kout, uint32_t* vout) {
-    __shared__ uint32_t wcount[SORT_WARPS][RADIX];  // per warp: digit counts, then running positions
-    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, tile = blockIdx.x;
-    for (uint32_t i = threadIdx.x; i < SORT_WARPS * RADIX; i += SORT_THREADS) (&wcount[0][0])[i] = 0u;
-    __syncthreads();
-    const unsigned long long wbase = (unsigned long long)tile * SORT_TILE + (unsigned long long)warp * SORT_WARP_RUN;
-    unsigned long long k[SORT_ITEMS];
-    uint32_t v[SORT_ITEMS], d[SORT_ITEMS];
-#pragma unroll
-    for (uint32_t j = 0; j < SORT_ITEMS; ++j) {
-        const unsigned long long at = wbase + j * 32u + lane;
-        const bool in = at < n;
-        k[j] = in ? kin[at] : 0ull;
-        v[j] = in ? vin[at] : 0u;
-        d[j] = in ? digit_of(k[j], shift) : RADIX;  // RADIX: no pair
-    }
-    // this warp's digit counts (one leader per digit group per step: no other writer)
-#pragma unroll
-    for (uint32_t j = 0; j < SORT_ITEMS; ++j) {
-        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d[j]);
-        if (d[j] < RADIX && lane == (uint32_t)(__ffs(peers) - 1)) wcount[warp][d[j]] += (uint32_t)__popc(peers);
-        __syncwarp();
-    }
-    __syncthreads();
-    // running positions: the tile's offset for the digit plus the counts of the warps before
-    {
-        const uint32_t dg = threadIdx.x;  // SORT_THREADS == RADIX
-        uint32_t run = offsets[(size_t)dg * ntiles + tile];
-        for (uint32_t w = 0; w < SORT_WARPS; ++w) {
-            const uint32_t c = wcount[w][dg];
-            wcount[w][dg] = run;
-            run += c;
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (uint32_t j = 0; j < SORT_ITEMS; ++j) {
-        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d[j]);
-        if (d[j] < RADIX) {
-            const uint32_t pos = wcount[warp][d[j]] + (uint32_t)__popc(peers & ((1u << lane) - 1u));
-            kout[pos] = k[j];
-            vout[pos] = v[j];
-        }
-        __syncwarp();
-        if (d[j] < RADIX && lane == (uint32_t)(__ffs(peers) - 1)) wcount[warp][d[j]] += (uint32_t)__popc(peers);
-        __syncwarp();
-    }
-}
-
-// --- scan
 
 // block-wide exclusive scan of one value per thread; returns the block total in *total
 __device__ __forceinline__ uint32_t block_excl(uint32_t x, uint32_t* wsum, uint32_t* total) {
@@ -135,6 +64,103 @@ __device__ __forceinline__ uint32_t block_excl(uint32_t x, uint32_t* wsum, uint3
     __syncthreads();
     return r;
 }
+
+// 1. digit counts of each tile, digit-major
+__global__ void __launch_bounds__(SORT_THREADS) k_sort_count(const unsigned long long* __restrict__ keys,
+                                                             unsigned long long n, uint32_t shift, uint32_t ntiles,
+                                                             uint32_t* counts) {
+    __shared__ uint32_t hist[RADIX];
+    const uint32_t tile = blockIdx.x;
+    hist[threadIdx.x] = 0u;  // SORT_THREADS == RADIX
+    __syncthreads();
+    const unsigned long long base = (unsigned long long)tile * SORT_TILE;
+    for (uint32_t i = threadIdx.x; i < SORT_TILE; i += SORT_THREADS) {
+        const unsigned long long at = base + i;
+        if (at < n) atomicAdd(&hist[digit_of(keys[at], shift)], 1u);
+    }
+    __syncthreads();
+    counts[(size_t)threadIdx.x * ntiles + tile] = hist[threadIdx.x];
+}
+
+// 3. stable placement of each tile's pairs from the scanned counts: the tile is first ordered by
+// digit in shared memory (stable), then written out so that consecutive threads store consecutive
+// pairs of one digit's run (coalesced stores instead of a scatter)
+__global__ void __launch_bounds__(SORT_THREADS) k_sort_place(const unsigned long long* __restrict__ kin,
+                                                             const uint32_t* __restrict__ vin, unsigned long long n,
+                                                             uint32_t shift, uint32_t ntiles,
+                                                             const uint32_t* __restrict__ offsets,
+                                                             unsigned long long* kout, uint32_t* vout) {
+    __shared__ uint32_t wcount[SORT_WARPS][RADIX];  // per warp: digit counts, then running positions
+    __shared__ unsigned long long sk[SORT_TILE];
+    __shared__ uint32_t sv[SORT_TILE];
+    __shared__ uint32_t tstart[RADIX];  // first position of each digit in the tile's digit order
+    __shared__ uint32_t gbase[RADIX];   // first output position of the tile's pairs of each digit
+    __shared__ uint32_t wsum[32];
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, tile = blockIdx.x;
+    for (uint32_t i = threadIdx.x; i < SORT_WARPS * RADIX; i += SORT_THREADS) (&wcount[0][0])[i] = 0u;
+    __syncthreads();
+    const unsigned long long tbase = (unsigned long long)tile * SORT_TILE;
+    const unsigned long long wbase = tbase + (unsigned long long)warp * SORT_WARP_RUN;
+    const uint32_t tcount = (uint32_t)min((unsigned long long)SORT_TILE, n - tbase);
+    unsigned long long k[SORT_ITEMS];
+    uint32_t v[SORT_ITEMS], d[SORT_ITEMS];
+#pragma unroll
+    for (uint32_t j = 0; j < SORT_ITEMS; ++j) {
+        const unsigned long long at = wbase + j * 32u + lane;
+        const bool in = at < n;
+        k[j] = in ? kin[at] : 0ull;
+        v[j] = in ? vin[at] : 0u;
+        d[j] = in ? digit_of(k[j], shift) : RADIX;  // RADIX: no pair
+    }
+    // this warp's digit counts (one leader per digit group per step: no other writer)
+#pragma unroll
+    for (uint32_t j = 0; j < SORT_ITEMS; ++j) {
+        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d[j]);
+        if (d[j] < RADIX && lane == (uint32_t)(__ffs(peers) - 1)) wcount[warp][d[j]] += (uint32_t)__popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // digit totals of the tile, their start in digit order, and each warp's running position
+    {
+        const uint32_t dg = threadIdx.x;  // SORT_THREADS == RADIX
+        uint32_t tot = 0;
+        for (uint32_t w = 0; w < SORT_WARPS; ++w) tot += wcount[w][dg];
+        uint32_t all;
+        const uint32_t start = block_excl(tot, wsum, &all);
+        tstart[dg] = start;
+        gbase[dg] = offsets[(size_t)dg * ntiles + tile];
+        uint32_t run = start;
+        for (uint32_t w = 0; w < SORT_WARPS; ++w) {
+            const uint32_t c = wcount[w][dg];
+            wcount[w][dg] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    // the tile in digit order (stable) in shared memory
+#pragma unroll
+    for (uint32_t j = 0; j < SORT_ITEMS; ++j) {
+        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d[j]);
+        if (d[j] < RADIX) {
+            const uint32_t pos = wcount[warp][d[j]] + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+            sk[pos] = k[j];
+            sv[pos] = v[j];
+        }
+        __syncwarp();
+        if (d[j] < RADIX && lane == (uint32_t)(__ffs(peers) - 1)) wcount[warp][d[j]] += (uint32_t)__popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < tcount; i += SORT_THREADS) {
+        const unsigned long long key = sk[i];
+        const uint32_t dg = digit_of(key, shift);
+        const uint32_t pos = gbase[dg] + (i - tstart[dg]);
+        kout[pos] = key;
+        vout[pos] = sv[i];
+    }
+}
+
+// --- scan
 
 // sum of each tile
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_sums(const uint32_t* __restrict__ in, unsigned long long n,
