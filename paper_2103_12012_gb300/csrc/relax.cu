@@ -33,8 +33,10 @@
 //      high-diameter graph) is latency-bound: there a queued vertex's row
 //      extents are loaded alongside its atomic, its entry goes straight into
 //      the other half of the selection arrays, a single warp scans the degrees
-//      of up to 32 vertices, and the read-first filter is dropped while most
-//      relaxations of the block reach the atomic;
+//      of up to 32 vertices, the read-first filter is dropped while most
+//      relaxations of the block reach the atomic, and a thread's message is
+//      sent at the start of the next sub-round (its atomic overlapping that
+//      sub-round's loads) or, after the last one, before F;
 //   F  settle the termination count and ring the doorbells of every unit
 //      that received a new vertex (and this unit's own if vertices are left).
 // Termination (Sec. III.D, the message counter of ToKa): `pending` counts
@@ -75,21 +77,19 @@ constexpr uint32_t MSG_CAP = 64;             // messages one warp can hold (msg_
 constexpr unsigned long long ROUND_RESERVE = 1ull << 41;
 static_assert(ROUND_RESERVE >= (unsigned long long)MAX_SUBROUNDS << 32, "reserve covers a round's activations");
 
+// release ordering for the writes before it (an inbox bit after its lowered word)
+__device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
 __device__ __forceinline__ uint32_t atom_and_acquire(uint32_t* p, uint32_t v) {
     uint32_t old;
     asm volatile("atom.acquire.gpu.global.and.b32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
     return old;
 }
 
-__device__ __forceinline__ uint32_t warp_min(uint32_t x) {
-    for (int o = 16; o > 0; o >>= 1) x = min(x, __shfl_xor_sync(0xFFFFFFFFu, x, o));
-    return x;
-}
-
-__device__ __forceinline__ uint32_t warp_sum(uint32_t x) {
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
-    return x;
-}
+// whole-warp reductions (one redux.sync instead of five dependent shuffles: a small sub-round
+// runs several of them between its barriers)
+__device__ __forceinline__ uint32_t warp_min(uint32_t x) { return __reduce_min_sync(0xFFFFFFFFu, x); }
+__device__ __forceinline__ uint32_t warp_sum(uint32_t x) { return __reduce_add_sync(0xFFFFFFFFu, x); }
 
 // bits of inbox word `wd` that belong to vertices in [lo, hi)
 __device__ __forceinline__ uint32_t range_mask(uint32_t wd, uint32_t lo, uint32_t hi) {
@@ -268,13 +268,10 @@ struct Smem {
     unsigned long long* st;  // [ST_N] block statistics
 };
 
-// Sets v's inbox bit (the caller has fenced the lowered word before it); a new bit
-// counts as an activation and, in static mode, marks v's unit for a doorbell.
+// A new inbox bit for v: one activation, and in static mode a doorbell for v's unit.
 template <bool STATIC>
-__device__ __forceinline__ void inbox_set(const Ctx& c, uint32_t v, uint32_t my_q, const Smem& sm, uint32_t& lact,
-                                          uint32_t& n_rem) {
-    const uint32_t bit = 1u << (v & 31u);
-    if (atomicOr(&c.bitmap[v >> 5], bit) & bit) return;
+__device__ __forceinline__ void inbox_count(const Ctx& c, uint32_t v, uint32_t my_q, const Smem& sm, uint32_t& lact,
+                                            uint32_t& n_rem) {
     ++lact;
     if (STATIC) {
         const uint32_t p = v / c.B;
@@ -282,6 +279,16 @@ __device__ __forceinline__ void inbox_set(const Ctx& c, uint32_t v, uint32_t my_
         if (q != my_q) ++n_rem;
         atomicOr(&sm.touched[q >> 5], 1u << (q & 31u));
     }
+}
+
+// Sets v's inbox bit (the caller has fenced the lowered word before it); a new bit
+// counts as an activation and, in static mode, marks v's unit for a doorbell.
+template <bool STATIC>
+__device__ __forceinline__ void inbox_set(const Ctx& c, uint32_t v, uint32_t my_q, const Smem& sm, uint32_t& lact,
+                                          uint32_t& n_rem) {
+    const uint32_t bit = 1u << (v & 31u);
+    if (atomicOr(&c.bitmap[v >> 5], bit) & bit) return;
+    inbox_count<STATIC>(c, v, my_q, sm, lact, n_rem);
 }
 
 // Batched buckets: files v (distance d, never below the current fine bucket bkb) in its
@@ -612,6 +619,13 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
         // upper half of the selection arrays: `base` is where this sub-round's are.
         const uint32_t H = c.tile >> 1;
         uint32_t base = 0;
+        // A small sub-round is a chain of dependent global accesses, and a message (an inbox
+        // bit in another unit, or in this one when the local queue is full) would add two
+        // more to the thread that sends it.  So a thread of a small sub-round keeps its one
+        // message (dv) and sends it at the start of the next sub-round, where the atomic's
+        // round trip overlaps that sub-round's own loads; what is left is sent before the
+        // round settles its termination count.
+        uint32_t dv = NONE;
         for (uint32_t sub = 0;; ++sub) {
             if (nsel <= 32u) {  // one warp's scan, one barrier
                 if (tid < 32u) {
@@ -662,6 +676,14 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
             // lifting, the batch's searches interleaved).
             uint32_t lact = 0, bad = 0;
             uint32_t n_ai = 0, n_rem = 0;  // statistics: atomics | improved << 16, remote activations
+            uint32_t d_old = 0, d_bit = 0, d_v = NONE;  // the message held over from the last sub-round
+            if (STATIC && dv != NONE) {
+                fence_acq_rel();  // its lowered word (an atomic that has returned) before its bit
+                d_v = dv;
+                dv = NONE;
+                d_bit = 1u << (d_v & 31u);
+                d_old = atomicOr(&c.bitmap[d_v >> 5], d_bit);  // the result is read at the end
+            }
             const bool consec = te >= 32u * nsel;
             // The read-first filter adds an L2 round trip before each atomic.  A sub-round
             // of at most one edge per thread is latency-bound, so the persistent solve drops
@@ -716,8 +738,7 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
                                 } else if constexpr (BK) {
                                     bucket_file<W>(c, v, cand, bkb, sc, lact);
                                 } else {
-                                    __threadfence();  // the lowered word before its inbox bit
-                                    inbox_set<STATIC>(c, v, my_q, sm, lact, n_rem);
+                                    dv = v;  // sent by the next sub-round (or after the last)
                                 }
                             }
                         }
@@ -855,6 +876,7 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
                 }
                 if (held && mn) push_out();  // age criterion: the end of the sub-round
             }
+            if (STATIC && d_v != NONE && !(d_old & d_bit)) inbox_count<STATIC>(c, d_v, my_q, sm, lact, n_rem);
             lact = warp_sum(lact);
             bad = __reduce_or_sync(0xFFFFFFFFu, bad);
             {
@@ -889,6 +911,20 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
             }
             if (tid == 0) sm.st[ST_VERTS] += nlq;
             nsel = nlq;
+            __syncthreads();
+        }
+        if (STATIC) {  // the messages of the last sub-round
+            uint32_t lact = 0, n_rem = 0;
+            if (dv != NONE) {
+                fence_acq_rel();
+                inbox_set<STATIC>(c, dv, my_q, sm, lact, n_rem);
+            }
+            lact = warp_sum(lact);
+            n_rem = warp_sum(n_rem);
+            if (lane == 0) {
+                if (lact) atomicAdd(&sc.act, (unsigned long long)lact);
+                if (n_rem) atomicAdd(&sm.st[ST_REMOTE], (unsigned long long)n_rem);
+            }
             __syncthreads();
         }
     }
