@@ -86,10 +86,23 @@ __device__ __forceinline__ uint32_t atom_and_acquire(uint32_t* p, uint32_t v) {
     return old;
 }
 
-// whole-warp reductions (one redux.sync instead of five dependent shuffles: a small sub-round
-// runs several of them between its barriers)
-__device__ __forceinline__ uint32_t warp_min(uint32_t x) { return __reduce_min_sync(0xFFFFFFFFu, x); }
-__device__ __forceinline__ uint32_t warp_sum(uint32_t x) { return __reduce_add_sync(0xFFFFFFFFu, x); }
+// Whole-warp reductions: one redux.sync (RX) or five dependent shuffles.  The persistent solve
+// takes redux.sync (a small sub-round runs several of them between its barriers: grid 4096^2
+// 48.5 against 49.3 ms); the batched kernel keeps the shuffles, which leave it fewer spills
+// (47.0 against 47.2 ms on the 512-graph batch).
+template <bool RX = true>
+__device__ __forceinline__ uint32_t warp_min(uint32_t x) {
+    if constexpr (RX) return __reduce_min_sync(0xFFFFFFFFu, x);
+    for (int o = 16; o > 0; o >>= 1) x = min(x, __shfl_xor_sync(0xFFFFFFFFu, x, o));
+    return x;
+}
+
+template <bool RX = true>
+__device__ __forceinline__ uint32_t warp_sum(uint32_t x) {
+    if constexpr (RX) return __reduce_add_sync(0xFFFFFFFFu, x);
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
+    return x;
+}
 
 // bits of inbox word `wd` that belong to vertices in [lo, hi)
 __device__ __forceinline__ uint32_t range_mask(uint32_t wd, uint32_t lo, uint32_t hi) {
@@ -437,7 +450,7 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
                 sm.list_v[i] = beg;
                 sm.sel_pref[i] = deg;
             }
-            myproc = warp_sum(myproc);
+            myproc = warp_sum<!BK>(myproc);
             if (lane == 0 && myproc) atomicAdd(&sc.nclaim, myproc);
             if (tid == 0) sc.bk_cnt[slot] -= nsel;
         } else if (op == OP_SPLIT) {
@@ -456,7 +469,7 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
                 else
                     move(bm, from, v, b, kn);
             });
-            gone = warp_sum(gone);
+            gone = warp_sum<!BK>(gone);
             if (lane == 0 && gone) atomicSub(&sc.bk_cnt[from], gone);
             __syncthreads();
             if (tid == 0) {
@@ -473,7 +486,7 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
                 for_each_set(ov, [&](bool ok, uint32_t v) {
                     uint32_t d = ok ? dist(v) : 0xFFFFFFFFu;
                     if (ok && W::bucket(d, c.delta) / BK_NB <= k0) d = 0xFFFFFFFFu;  // stale
-                    const uint32_t m = warp_min(d);
+                    const uint32_t m = warp_min<!BK>(d);
                     if (lane == 0 && m != 0xFFFFFFFFu) atomicMin(&sc.dmin, m);
                 });
                 __syncthreads();
@@ -495,7 +508,7 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
                     atomicMin(&sc.bk_ovmin, kc);  // stays in the overflow
                 }
             });
-            gone = warp_sum(gone);
+            gone = warp_sum<!BK>(gone);
             if (lane == 0 && gone) atomicSub(&sc.bk_cnt[BK_OV], gone);
             __syncthreads();
             if (tid == 0 && op == OP_FLUSH_NEW) {
@@ -530,7 +543,7 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
                     ds[g] = i0 + 32u * g < total ? (uint32_t)(__ldcg(&c.packed[vs[g]]) >> 32) : 0xFFFFFFFFu;
                     bm = min(bm, ds[g]);
                 }
-                bm = warp_min(bm);  // lane 0's first element is valid: bm is a distance
+                bm = warp_min<!BK>(bm);  // lane 0's first element is valid: bm is a distance
                 if (lane == 0) atomicMin(&sc.dmin, bm);
                 const uint32_t bound =
                     policy_bound<W>(min(bm, *(volatile uint32_t*)&sc.dmin), c.delta, c.policy, sc.nf);
@@ -604,7 +617,7 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
                 sm.list_v[i] = beg;
                 sm.sel_pref[i] = deg;
             }
-            myclaim = warp_sum(myclaim);
+            myclaim = warp_sum<!BK>(myclaim);
             if (lane == 0 && myclaim) atomicAdd(&sc.nclaim, myclaim);
         }
     }
@@ -877,10 +890,11 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
                 if (held && mn) push_out();  // age criterion: the end of the sub-round
             }
             if (STATIC && d_v != NONE && !(d_old & d_bit)) inbox_count<STATIC>(c, d_v, my_q, sm, lact, n_rem);
-            lact = warp_sum(lact);
+            lact = warp_sum<!BK>(lact);
             bad = __reduce_or_sync(0xFFFFFFFFu, bad);
             {
-                const uint32_t wa = warp_sum(n_ai & 0xFFFFu), wi = warp_sum(n_ai >> 16), wr = warp_sum(n_rem);
+                const uint32_t wa = warp_sum<!BK>(n_ai & 0xFFFFu), wi = warp_sum<!BK>(n_ai >> 16);
+                const uint32_t wr = warp_sum<!BK>(n_rem);
                 if (lane == 0) {
                     if (wa) atomicAdd(&sm.st[ST_ATOMICS], (unsigned long long)wa);
                     if (wi) atomicAdd(&sm.st[ST_IMPROVED], (unsigned long long)wi);
@@ -919,8 +933,8 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
                 fence_acq_rel();
                 inbox_set<STATIC>(c, dv, my_q, sm, lact, n_rem);
             }
-            lact = warp_sum(lact);
-            n_rem = warp_sum(n_rem);
+            lact = warp_sum<!BK>(lact);
+            n_rem = warp_sum<!BK>(n_rem);
             if (lane == 0) {
                 if (lact) atomicAdd(&sc.act, (unsigned long long)lact);
                 if (n_rem) atomicAdd(&sm.st[ST_REMOTE], (unsigned long long)n_rem);
