@@ -510,6 +510,29 @@ def test_solve_small_and_general_subround_mix(sssp, f32, P, opts):
     check_solve(sssp, g, ref, [0, 9, 5, 4000], sssp.options(**opts))
 
 
+@pytest.mark.parametrize("f32", [False, True])
+@pytest.mark.parametrize("P,opts", [(12, dict(tile=32, delta=1e6)), (40, dict(tile=64, split=4, delta=300)),
+                                    (148, dict(tile=1024, split=2, delta=3000)),
+                                    (12, dict(tile=32, msg_buffer=8, delta=1e6)),
+                                    (7, dict(tile=32, threads=128, delta=50))])
+def test_grid_wavefront_messages_of_small_subrounds(sssp, f32, P, opts):
+    """A random-weight grid from a corner, the middle and the far corner: the wavefront runs
+    sub-rounds of a few vertices on the small path, whose messages into the next unit (and,
+    with tiles of 32 or 64, into this unit once its local queue is full) are sent by the next
+    sub-round or before the round settles; also on the locality layout with hubs."""
+    side = 120
+    g0 = gg.grid(gg.BASE_SEED + 620, side, side, 1, 1000)
+    w = (g0.w.astype(np.float32) * np.float32(0.01)) if f32 else g0.w
+    o = dict(opts)
+    if f32 and o["delta"] < 1e6:
+        o["delta"] *= 0.01
+    ref = oracle.csr(g0.V, g0.src, g0.dst, w)
+    g = sssp.build_csr(g0.V, g0.src, g0.dst, w, partitions=P)
+    srcs = [0, side * (side // 2) + side // 2, side * side - 1]
+    check_solve(sssp, g, ref, srcs, sssp.options(**o))
+    check_solve(sssp, sssp.layout(g), ref, srcs, sssp.options(hub_count=16, **o))
+
+
 def test_solve_overflow_status(sssp):
     w = np.array([0xFFFFFFFE, 2, 1], np.uint32)
     src, dst = np.array([0, 1, 0], np.uint32), np.array([1, 2, 3], np.uint32)
