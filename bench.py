@@ -710,7 +710,8 @@ def extras_batched(sssp, dev, rank=0, world=1):
     ms_prob = _time_ms(per_problem, 1)
     return {"workload": "512 graphs (ER deg 8 / R-MAT ef 8, n = 2^U(10,17)), 16 sources each",
             "problems": n_prob, "edges_total": int(edges),
-            "options": {"delta": tuned.delta, "tile": tuned.tile or 1024, "autotuned": True},
+            "options": {"delta": tuned.delta, "tile": tuned.tile or 1024, "threads": tuned.threads or 512,
+                        "autotuned": True},
             "graph_replay_ms": round(ms_plan, 3), "solves_per_s": round(n_prob / ms_plan * 1e3, 1),
             "reached_edges": E_r, "reached_vertices": V_r, "edges_scanned": stats["edges_scanned"],
             "work_inflation": round(stats["edges_scanned"] / max(E_r, 1), 3),
@@ -1032,11 +1033,12 @@ def profile_case(which):
         torch.cuda.synchronize()
         print("all", g.E, h.E, gp.E, float(gr.abs().sum()))
     elif which == "batched-full":
-        # the full 512-graph, 16-source batch at the schedule the bench's tuner picks (delta 8, tile 1024)
+        # the full 512-graph, 16-source batch at the schedule the bench's tuner picks (1024-thread
+        # blocks, tile 2048, delta 12)
         graphs0, sources = gg.workload_batch512()
         graphs = [sssp.build_csr(x.V, x.src, x.dst, x.w) for x in graphs0]
         del graphs0
-        b = sssp.Batch(graphs, sources, sssp.options(delta=8, tile=1024))
+        b = sssp.Batch(graphs, sources, sssp.options(threads=1024, tile=2048, delta=12))
         for _ in range(2):
             b.solve()
         st, stats = b.status()

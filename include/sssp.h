@@ -89,7 +89,8 @@ typedef struct {
 /* Tuning knobs; a zero field means "default".  None of them changes the
  * result, only the schedule. */
 typedef struct {
-    uint32_t threads;      /* threads per block of the relaxation kernel: 128..512, multiple of 32 (default 512) */
+    uint32_t threads;      /* threads per block of the relaxation kernel: a multiple of 32, 128..512 for
+                              sssp_solve, 128..1024 for sssp_solve_batched (default 512) */
     uint32_t blocks_per_sm;/* persistent blocks per SM (default: as many as fit) */
     uint32_t tile;         /* most vertices one block takes from its inbox per round: 32..4096 (default 1024) */
     uint32_t split;        /* blocks sharing one partition, each owning a sub-block of its vertices (default 1) */

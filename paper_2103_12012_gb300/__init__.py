@@ -500,9 +500,11 @@ class Batch:
         _check(lib().sssp_solve_batched(ctypes.byref(self.c), ctypes.byref(self.opts), _ptr(self.ws), self.ws_bytes,
                                         _stream(stream)), "sssp_solve_batched")
 
-    def autotune(self, deltas=(2, 4, 8, 16, 32, 64), tiles=(256, 512, 1024, 2048), stream=None):
-        """Choose the batched kernel's bucket width and tile by timing sssp_solve_batched on this batch
-        (coordinate search: delta, then tile).  Sets self.opts and returns (options, ms)."""
+    def autotune(self, deltas=(2, 4, 8, 16, 32, 64), tiles=(256, 512, 1024, 2048), threads=(512, 1024),
+                 stream=None):
+        """Choose the batched kernel's bucket width, tile and block size by timing sssp_solve_batched on
+        this batch (coordinate search: delta; then tile and block size together; then delta again at
+        3/4, 5/4 and 3/2 of the best).  Sets self.opts and returns (options, ms)."""
         torch = _torch()
 
         def run(o):
@@ -522,16 +524,23 @@ class Batch:
 
         base = self.opts
         best, best_ms = base, run(base)
+
+        def consider(o):
+            nonlocal best, best_ms
+            ms = run(o)
+            if ms < best_ms:
+                best, best_ms = o, ms
+
         for d in deltas:
-            o = options(threads=base.threads, tile=base.tile, delta=d)
-            ms = run(o)
-            if ms < best_ms:
-                best, best_ms = o, ms
-        for t in tiles:
-            o = options(threads=best.threads, tile=t, delta=best.delta)
-            ms = run(o)
-            if ms < best_ms:
-                best, best_ms = o, ms
+            consider(options(threads=base.threads, tile=base.tile, delta=d))
+        d0 = best.delta
+        for th in threads:
+            for t in tiles:
+                consider(options(threads=th, tile=t, delta=d0))
+        b0 = best
+        for f in (0.75, 1.25, 1.5):
+            d = b0.delta * f if self.wtype == W_F32 else max(1, round(b0.delta * f))
+            consider(options(threads=b0.threads, tile=b0.tile, delta=d))
         self.opts = best
         if self.plan is not None:
             lib().sssp_batch_plan_destroy(self.plan)

@@ -527,7 +527,7 @@ sssp_status prepare_batch(const sssp_batch* b, const sssp_options* opt, void* ws
     Resolved r;
     BatchTables t;
     if (!ws || !aligned16(ws) || !resolve(opt, b ? b->wtype : 0, &r) || !build_tables(b, &t)) return SSSP_EINVAL;
-    if (r.threads > SOLVE_MAX_THREADS) return SSSP_EINVAL;
+    if (r.threads > BATCH_MAX_THREADS) return SSSP_EINVAL;
     const BatchWs L = batch_layout(b->n_problems, t.total_out, t.total_words);
     if (ws_bytes < L.total) return SSSP_ENOMEM;
     char* base = static_cast<char*>(ws);

@@ -60,7 +60,8 @@ struct SolveLaunch {
     TrishlaJob prune;
 };
 
-constexpr uint32_t SOLVE_MAX_THREADS = 512;  // block size limit of the solve kernel
+constexpr uint32_t SOLVE_MAX_THREADS = 512;   // block size limit of the solve kernel
+constexpr uint32_t BATCH_MAX_THREADS = 1024;  // block size limit of the batched kernel
 size_t relax_smem_bytes(uint32_t tile, uint32_t Q, bool msgs);
 cudaError_t relax_max_blocks_per_sm(int wtype, uint32_t threads, uint32_t tile, uint32_t Q, int* out,
                                     bool prune = false, bool msgs = false, bool hubs = false);

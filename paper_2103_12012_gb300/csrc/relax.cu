@@ -1259,10 +1259,13 @@ __global__ void __launch_bounds__(SOLVE_MAX_THREADS, 4) k_solve(SolveLaunch L) {
     flush_stats(L.hdr, sm.st);
 }
 
-// K5: persistent, dynamic: blocks pull whole problems from a work queue (four
-// 512-thread blocks per SM, as for K4).
+// K5: persistent, dynamic: blocks pull whole problems from a work queue.  Compiled for
+// 2 x 1024 threads per SM (the register budget of 4 x 512): two 1024-thread blocks hold half the
+// problems in flight, and so half the distance state competing for L2, with twice the threads on
+// each problem's rounds (the 512-graph batch: 44.2 ms at tile 2048 against 47.0 ms with four
+// 512-thread blocks at tile 1024).
 template <class W>
-__global__ void __launch_bounds__(SOLVE_MAX_THREADS, 4) k_batched(BatchLaunch L) {
+__global__ void __launch_bounds__(BATCH_MAX_THREADS, 2) k_batched(BatchLaunch L) {
     extern __shared__ uint32_t dsm[];
     __shared__ uint32_t wsum[32];
     __shared__ Scalars sc;

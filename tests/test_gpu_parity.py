@@ -661,7 +661,8 @@ def test_batched_equals_single_solves(sssp):
         assert torch.equal(bd, dist[i]) and torch.equal(bp, pred[i])
 
 
-@pytest.mark.parametrize("threads,tile", [(128, 1024), (128, 64), (256, 256), (256, 4096), (512, 512), (384, 32)])
+@pytest.mark.parametrize("threads,tile", [(128, 1024), (128, 64), (256, 256), (256, 4096), (512, 512), (384, 32),
+                                          (1024, 2048), (1024, 64), (1024, 4096), (768, 1024), (992, 100)])
 def test_batched_block_sizes(sssp, threads, tile):
     """The batched kernel with every block size and tile: blocks smaller or larger than the tile
     and than half of it (the small sub-round path keeps its entries in tile halves)."""
@@ -680,7 +681,8 @@ def test_batched_block_sizes(sssp, threads, tile):
 
 
 @pytest.mark.parametrize("f32", [False, True])
-@pytest.mark.parametrize("opts", [dict(delta=1e6), dict(delta=1e6, tile=256), dict(delta=1)])
+@pytest.mark.parametrize("opts", [dict(delta=1e6), dict(delta=1e6, tile=256), dict(delta=1),
+                                  dict(delta=1e6, threads=1024, tile=2048)])
 def test_batched_small_and_general_subround_mix(sssp, f32, opts):
     src, dst, w = _subround_graph(f32)
     ref = oracle.csr(6000, src, dst, w)
