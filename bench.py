@@ -1034,11 +1034,11 @@ def profile_case(which):
         print("all", g.E, h.E, gp.E, float(gr.abs().sum()))
     elif which == "batched-full":
         # the full 512-graph, 16-source batch at the schedule the bench's tuner picks (1024-thread
-        # blocks, tile 2048, delta 12)
+        # blocks, tile 2048, delta 16)
         graphs0, sources = gg.workload_batch512()
         graphs = [sssp.build_csr(x.V, x.src, x.dst, x.w) for x in graphs0]
         del graphs0
-        b = sssp.Batch(graphs, sources, sssp.options(threads=1024, tile=2048, delta=12))
+        b = sssp.Batch(graphs, sources, sssp.options(threads=1024, tile=2048, delta=16))
         for _ in range(2):
             b.solve()
         st, stats = b.status()

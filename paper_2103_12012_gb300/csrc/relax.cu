@@ -65,8 +65,10 @@ constexpr int GATHER_G = 2;                   // queued vertices a lane enumerat
 constexpr uint32_t IDLE_BACKOFF_MAX_NS = 1024;  // longest sleep of a block with no dirty unit
 constexpr uint64_t PRUNE_IDLE_NS = 20000;      // idle this long before a block runs Trishla chunks
 // batched distance buckets: BK_NB fine buckets of width delta (the current coarse bucket),
-// BK_NC coarse buckets of width BK_NB * delta after it, then one overflow
-constexpr uint32_t BK_NB = 16, BK_NC = 16, BK_OV = BK_NB + BK_NC, BK_SLOTS = BK_NB + BK_NC + 1;
+// BK_NC coarse buckets of width BK_NB * delta after it, then one overflow.  8 + 8 keeps a
+// problem's bitmaps at 17 bits a vertex (half of 16 + 16, whose state in flight misses L2 more):
+// the 512-graph batch 41.6 ms against 42.6 ms, each at its best delta.
+constexpr uint32_t BK_NB = 8, BK_NC = 8, BK_OV = BK_NB + BK_NC, BK_SLOTS = BK_NB + BK_NC + 1;
 constexpr int EDGE_BATCH = 3;                // edges in flight per thread in phase E (measured: 2-4 similar)
 constexpr uint32_t MSG_CAP = 64;             // messages one warp can hold (msg_buffer <= 32, plus one batch of 32)
 // Termination counts a round reserves before any of its inbox bits can be visible.  A round
