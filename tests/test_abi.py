@@ -80,7 +80,7 @@ def test_workspace_sizes_scale(L):
     assert 8 * 4194304 <= one < 8 * 4194304 * 1.1
     assert abs(eight - 8 * one) < 8 * 4096
     assert L.sssp_build_csr_workspace_size(1000, 5000) > 5000 * 36
-    assert L.sssp_backward_workspace_size(1000, 5000, 3) >= 3 * 1000 * 13 + 5000 * 8
+    assert L.sssp_backward_workspace_size(1000, 5000, 3) >= 3 * 1000 * 17 + 5000 * 8
 
 
 def test_batch_tables_checked_on_host(L):
