@@ -231,10 +231,13 @@ def test_rmat18_f32_forward_backward(sssp, monkeypatch, tmp_path):
 
 
 def test_batch512_sampled_and_certified(sssp):
+    """The full batch in the schedule the benchmark times (the batch tuner's choice: block size,
+    tile and bucket width), replayed from its CUDA graph."""
     graphs0, sources = gg.workload_batch512()
     graphs = [oracle.csr_of(g) for g in graphs0]
     del graphs0
     b = sssp.Batch(graphs, sources)
+    b.autotune()
     b.make_plan()
     b.replay()
     st, stats = b.status()
