@@ -732,3 +732,40 @@ def test_autograd_function(sssp):
     rp = np.stack([oracle.dijkstra(ref, int(s))[1] for s in srcs_np])
     rg = oracle.tree_grad(ref, rd, rp, gup.cpu().numpy())
     assert np.allclose(w.grad.cpu().numpy(), rg, rtol=1e-5, atol=1e-6 * np.abs(rg).max())
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_random_schedules_match_the_oracle(sssp, seed):
+    """A seeded sweep of schedules (block size, tile, split, width, policy, hubs, message
+    buffering, layout, weight type) on random graphs of random size and partitioning: every
+    combination gives the oracle's distances and predecessors."""
+    rng = np.random.default_rng(9000 + seed)
+    V = int(rng.integers(40, 4000))
+    E = int(rng.integers(V, 10 * V))
+    f32 = bool(rng.integers(0, 2))
+    src, dst, w = raw_graph(9100 + seed, V, E, f32=f32)
+    ref = oracle.csr(V, src, dst, w)
+    P = int(rng.integers(1, min(148, V) + 1))
+    g = sssp.build_csr(V, src, dst, w, partitions=P)
+    lay = bool(rng.integers(0, 2))
+    if lay:
+        g = sssp.layout(g)
+    delta = float(rng.choice([0.0, 1.0, 3.0, 17.0, 1e6]))
+    if f32 and delta:
+        delta *= 0.01
+    o = sssp.options(threads=int(rng.choice([128, 256, 384, 512])), tile=int(rng.choice([32, 100, 512, 1024, 4096])),
+                     split=int(rng.integers(1, 4)), delta=delta, policy=int(rng.integers(0, 4)),
+                     msg_buffer=int(rng.choice([0, 0, 1, 8, 32])), hub_count=int(rng.choice([0, 4, 64])) if lay else 0)
+    sources = sorted(set(int(x) for x in rng.integers(0, V, 3)))
+    check_solve(sssp, g, ref, sources, o)
+    # the same graph in a batch, in a random batched schedule
+    bo = sssp.options(threads=int(rng.choice([128, 512, 1024])), tile=int(rng.choice([64, 1024, 2048])),
+                      delta=delta)
+    b = sssp.Batch([ref], [np.array(sources, np.uint32)], bo)
+    b.solve()
+    st, _ = b.status()
+    assert st == sssp.SSSP_OK
+    for i, s in enumerate(sources):
+        d, p, _ = oracle.dijkstra(ref, s)
+        bd, bp = b.result(i)
+        assert np.array_equal(u32(bd), d.view(np.uint32)) and np.array_equal(u32(bp), p), (seed, i)
