@@ -69,7 +69,11 @@ constexpr uint64_t PRUNE_IDLE_NS = 20000;      // idle this long before a block 
 // problem's bitmaps at 17 bits a vertex (half of 16 + 16, whose state in flight misses L2 more):
 // the 512-graph batch 41.6 ms against 42.6 ms, each at its best delta.
 constexpr uint32_t BK_NB = 8, BK_NC = 8, BK_OV = BK_NB + BK_NC, BK_SLOTS = BK_NB + BK_NC + 1;
-constexpr int EDGE_BATCH = 3;                // edges in flight per thread in phase E (measured: 2-4 similar)
+// edges in flight per thread in phase E: 3, and 4 in the hub variant (layout graphs with hubs,
+// whose hub rows take the consecutive-edge mode): R-MAT scale 22 7.03 against 7.14 ms, while 4
+// everywhere would slow the grid (50.6 against 45.1 ms) and 2 slows both
+constexpr int EDGE_BATCH = 3;
+constexpr int EDGE_BATCH_HUBS = 4;
 constexpr uint32_t MSG_CAP = 64;             // messages one warp can hold (msg_buffer <= 32, plus one batch of 32)
 // Termination counts a round reserves before any of its inbox bits can be visible.  A round
 // runs at most MAX_SUBROUNDS sub-rounds; a sub-round relaxes the edges of distinct vertices,
@@ -329,6 +333,7 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
                                 const Smem& sm) {
     static_assert(!(STATIC && BK), "distance buckets belong to the batched kernel");
     static_assert(!HELD || STATIC, "message buffering belongs to the persistent solve");
+    constexpr int EB = HUBS ? EDGE_BATCH_HUBS : EDGE_BATCH;
     const uint32_t T = blockDim.x, tid = threadIdx.x, lane = tid & 31u;
     Scalars& sc = *sm.sc;
     if (tid == 0) {
@@ -681,14 +686,14 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
                 __syncthreads();
             }
 
-            // ---- E: relax all out-edges, edge-parallel.  Each thread keeps
-            // EDGE_BATCH edges in flight together: all CSR loads, then all read-first
-            // filters, then all atomics.  Its edges are a block-width apart (lanes read
-            // consecutive edges: coalesced across short rows) unless the taken vertices
-            // average 32 edges or more (hubs), where a warp takes consecutive edges, its lane
-            // l the ones 32 apart, and one search of the degree prefix serves the lane's
-            // batch.  Row of edge k: the largest a < nsel with sel_pref[a] <= k (binary
-            // lifting, the batch's searches interleaved).
+            // ---- E: relax all out-edges, edge-parallel.  Each thread keeps EB edges
+            // (EDGE_BATCH; EDGE_BATCH_HUBS in the hub variant) in flight together: all CSR
+            // loads, then all read-first filters, then all atomics.  Its edges are a
+            // block-width apart (lanes read consecutive edges: coalesced across short rows)
+            // unless the taken vertices average 32 edges or more (hubs), where a warp takes
+            // consecutive edges, its lane l the ones 32 apart, and one search of the degree
+            // prefix serves the lane's batch.  Row of edge k: the largest a < nsel with
+            // sel_pref[a] <= k (binary lifting, the batch's searches interleaved).
             uint32_t lact = 0, bad = 0;
             uint32_t n_ai = 0, n_rem = 0;  // statistics: atomics | improved << 16, remote activations
             uint32_t d_old = 0, d_bit = 0, d_v = NONE;  // the message held over from the last sub-round
@@ -705,7 +710,7 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
             // the filter there while this block's relaxations mostly reach the atomic (at
             // least one atomic per four edges so far: wavefront graphs such as grids).
             const bool filt = BK || te > T || sm.st[ST_ATOMICS] * 4u < sm.st[ST_EDGES];
-            // consecutive mode: a warp takes 32 * EDGE_BATCH consecutive edges and lane l edges
+            // consecutive mode: a warp takes 32 * EB consecutive edges and lane l edges
             // l, l + 32, ... of them, so every load instruction reads 32 consecutive words (lane l
             // taking 3 adjacent edges spreads each load over 384 bytes: 1.5% slower on R-MAT)
             const uint32_t kstep = consec ? 32u : T;
@@ -773,17 +778,17 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
                 };
                 // with held messages the warp's lanes stay together (ballots): the trip count follows
                 // lane 0's first edge, and lanes past the end carry no edge
-                const uint32_t kwarp0 = consec ? (tid & ~31u) * EDGE_BATCH : (tid & ~31u);
-                for (uint32_t k0 = consec ? (tid & ~31u) * EDGE_BATCH + lane : tid, kw = kwarp0; (held ? kw : k0) < te;
-                     k0 += EDGE_BATCH * T, kw += EDGE_BATCH * T) {
-                    uint32_t vv[EDGE_BATCH], cc[EDGE_BATCH], aa[EDGE_BATCH];
+                const uint32_t kwarp0 = consec ? (tid & ~31u) * EB : (tid & ~31u);
+                for (uint32_t k0 = consec ? (tid & ~31u) * EB + lane : tid, kw = kwarp0; (held ? kw : k0) < te;
+                     k0 += EB * T, kw += EB * T) {
+                    uint32_t vv[EB], cc[EB], aa[EB];
     #pragma unroll
-                    for (int j = 0; j < EDGE_BATCH; ++j) aa[j] = 0;
+                    for (int j = 0; j < EB; ++j) aa[j] = 0;
                     if (consec) {
                         for (uint32_t st = top; st; st >>= 1)
                             if (aa[0] + st < nsel && sm.sel_pref[aa[0] + st] <= k0) aa[0] += st;
     #pragma unroll
-                        for (int j = 1; j < EDGE_BATCH; ++j) {  // step over row ends; sel_pref[nsel] = te
+                        for (int j = 1; j < EB; ++j) {  // step over row ends; sel_pref[nsel] = te
                             uint32_t a = aa[j - 1];
                             while (a + 1u < nsel && sm.sel_pref[a + 1u] <= k0 + (uint32_t)j * kstep) ++a;
                             aa[j] = a;
@@ -791,14 +796,14 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
                     } else {
                         for (uint32_t st = top; st; st >>= 1) {
     #pragma unroll
-                            for (int j = 0; j < EDGE_BATCH; ++j) {
+                            for (int j = 0; j < EB; ++j) {
                                 const uint32_t m = aa[j] + st;
                                 if (m < nsel && sm.sel_pref[m] <= k0 + (uint32_t)j * T) aa[j] = m;
                             }
                         }
                     }
     #pragma unroll
-                    for (int j = 0; j < EDGE_BATCH; ++j) {
+                    for (int j = 0; j < EB; ++j) {
                         const uint32_t k = k0 + (uint32_t)j * kstep;
                         vv[j] = NONE;
                         if (k < te) {
@@ -808,9 +813,9 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
                             cc[j] = __ldg(&c.w[e]);  // the weight, until it becomes the candidate below
                         }
                     }
-                    unsigned long long cur[EDGE_BATCH];
+                    unsigned long long cur[EB];
     #pragma unroll
-                    for (int j = 0; j < EDGE_BATCH; ++j) {
+                    for (int j = 0; j < EB; ++j) {
                         cur[j] = 0;
                         if (vv[j] == NONE) continue;
                         if (!W::weight_ok(cc[j]) || vv[j] >= c.V) {
@@ -828,7 +833,7 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
                     }
                     uint32_t improved = 0;
     #pragma unroll
-                    for (int j = 0; j < EDGE_BATCH; ++j) {
+                    for (int j = 0; j < EB; ++j) {
                         if (vv[j] == NONE) continue;
                         const unsigned long long key = ((unsigned long long)cc[j] << 32) | sm.sel_v[aa[j]];
                         if (key < cur[j]) {
@@ -857,7 +862,7 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
                     uint32_t msgs = 0;  // improved vertices of other units, held for a push-out
                     if (held && improved) {
     #pragma unroll
-                        for (int j = 0; j < EDGE_BATCH; ++j) {
+                        for (int j = 0; j < EB; ++j) {
                             if (!(improved & (1u << j))) continue;
                             const uint32_t p = vv[j] / c.B;
                             if (p * c.split + (vv[j] - p * c.B) / c.Bq != my_q) msgs |= 1u << j;
@@ -869,7 +874,7 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
                         // with buckets the only reader is this block, after its barriers
                         if constexpr (!BK) __threadfence();
     #pragma unroll
-                        for (int j = 0; j < EDGE_BATCH; ++j) {
+                        for (int j = 0; j < EB; ++j) {
                             if (!(improved & (1u << j))) continue;
                             const uint32_t v = vv[j];
                             if constexpr (BK)
@@ -880,7 +885,7 @@ __device__ uint32_t relax_round(const Ctx& c, uint32_t lo, uint32_t hi, uint32_t
                     }
                     if (held) {
     #pragma unroll
-                        for (int j = 0; j < EDGE_BATCH; ++j) {
+                        for (int j = 0; j < EB; ++j) {
                             const bool has = (msgs >> j) & 1u;
                             const uint32_t ball = __ballot_sync(0xFFFFFFFFu, has);
                             if (has) mbuf[mn + (uint32_t)__popc(ball & ((1u << lane) - 1u))] = vv[j];
