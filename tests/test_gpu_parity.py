@@ -734,7 +734,7 @@ def test_autograd_function(sssp):
     assert np.allclose(w.grad.cpu().numpy(), rg, rtol=1e-5, atol=1e-6 * np.abs(rg).max())
 
 
-@pytest.mark.parametrize("seed", range(24))
+@pytest.mark.parametrize("seed", range(64))
 def test_random_schedules_match_the_oracle(sssp, seed):
     """A seeded sweep of schedules (block size, tile, split, width, policy, hubs, message
     buffering, layout, weight type) on random graphs of random size and partitioning: every
